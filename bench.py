@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Throughput of the ICWF time step (arXiv 1805.11169) on one GB300, as one JSON line.
+
+Workload: the Shin-Metiu proton-coupled electron transfer model at the paper's scale, electron grid
+1024 points on [-100, 100], proton grid 512 points on [-9.5, 9.5], N = 1024 trajectories,
+dt = 0.05 a.u., initial state sampled from |Psi0|^2 with seed 0 (synthetic inputs: model potential
+and BO states computed here).  A step is one full ICWF update of all N trajectories (velocities,
+positions, CWF propagation, matrix assembly, regularised Cholesky + RK4); observables are
+evaluated every 100 steps inside the timed region.  Metric: trajectory-steps/s = N * steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|bf16x3|tf32x3]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores (same metric)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+OBS_EVERY = 100
+MODES = {"fp64": (0, "f64", 1e-12), "bf16x3": (1, "mixed-bf16x3", 1e-8),
+         "tf32x3": (2, "mixed-tf32x3", 1e-8)}
+NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 (vector and DMMA alike), nominal
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fp64", choices=list(MODES))
+    ap.add_argument("--n-traj", type=int, default=1024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def make_workload(n_traj, cutoff):
+    from workloads import WORKLOADS
+    return WORKLOADS["sm_paper"](n_traj=n_traj, svd_rel_cutoff=cutoff)
+
+
+def workload_name(w):
+    return f"shin_metiu_{w.nx}x{w.nR}_N{w.n_traj}_dt{w.dt}"
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dist.init_process_group("nccl" if os.environ.get("ICWF_BENCH_GLOO") is None else "gloo")
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.f:
+            return None
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+
+def algorithmic_work(fam, w, K, mode):
+    """(amount, unit, bound) of algorithmic work per launch of a kernel family."""
+    N, nx, nR = w.n_traj, w.nx, w.nR
+    c = 16 if mode == "fp64" else 8
+    if fam == "assemble":
+        # Hermitian half of (K+1) Grams per side: 4 N^2 (K+1)(nx+nR) real flops
+        return 4.0 * N * N * (K + 1) * (nx + nR), "flop", "alu" if mode == "fp64" else "tensor"
+    if fam == "propagate":
+        return 2.0 * N * (nx + nR) * c, "byte", "hbm"
+    if fam == "cholesky":
+        return 4.0 / 3.0 * N ** 3, "flop", "alu"
+    if fam == "velocity":
+        return 2.0 * 4 * N * N * c, "byte", "hbm"
+    if fam == "rk4_matvec":
+        return 16.0 * N * N * (1 if True else 2), "byte", "hbm"
+    if fam == "chol_solve":
+        return 2 * 8.0 * N * N, "flop", "alu"
+    return None
+
+
+def roofline(prof, w, K, mode, peaks):
+    fam = max(prof, key=lambda f: prof[f][0])
+    ms, n = prof[fam]
+    work = algorithmic_work(fam, w, K, mode)
+    out = {"kernel": fam, "launches": n, "avg_ms": ms / max(n, 1)}
+    if work is None or n == 0:
+        return out
+    amount, unit, bound = work
+    rate = amount / (ms / n / 1e3)
+    if unit == "byte":
+        out.update(bound="hbm", achieved=rate / 1e9, peak=peaks.get("hbm_gbs"), unit="GB/s",
+                   peak_source="measured (MEASURED_PEAKS.json hbm_gbs)")
+    elif bound == "tensor":
+        out.update(bound="tensor", achieved=rate / 1e12, peak=peaks.get("bf16_tflops_sustained"),
+                   unit="TFLOP/s", peak_source="measured bf16 sustained (MEASURED_PEAKS.json)")
+    else:
+        out.update(bound="alu", achieved=rate / 1e12, peak=NOMINAL_FP64_TFLOPS, unit="TFLOP/s",
+                   peak_source="nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)")
+    if out.get("peak"):
+        out["frac"] = out["achieved"] / out["peak"]
+    out["traffic"] = None
+    return out
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, ws, local):
+    import numpy as np
+    import torch
+    import paper_1805_11169_gb300 as g
+
+    torch.cuda.set_device(local)
+    prec, dtype_name, cutoff = MODES[args.mode]
+    w = make_workload(args.n_traj, cutoff)
+    params = g.params_from(w, precision=prec)
+
+    sim = g.Icwf(params, w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, w.seed)
+    info = sim.info()
+    stream = torch.cuda.ExternalStream(sim.stream())
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(args.warmup):
+        sim.step(1)
+    g.icwf_profile_reset(sim.h)
+    g.icwf_profile_enable(sim.h, True)
+    launches0 = sim.info()["kernel_launches"]
+    barrier(ws)
+    torch.cuda.synchronize()
+    step_ms = []
+    with Clocks(local) as clk:
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(1)
+            if (s + 1) % OBS_EVERY == 0:
+                sim.observables()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(ws)
+    g.icwf_profile_enable(sim.h, False)
+    prof = g.icwf_profile_read(sim.h)
+    launches = sim.info()["kernel_launches"] - launches0
+    n_obs = args.steps // OBS_EVERY
+    obs_launches = 4 * n_obs
+    total_s = max_over_ranks(sum(step_ms) / 1e3, ws)
+    value = ws * w.n_traj * args.steps / total_s
+    sim.close()
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+    prof_step = {f: v for f, v in prof.items() if v[1] > 0 and f != "observables"}
+    rl = roofline(prof_step, w, info["rank"], args.mode, peaks)
+
+    out = {
+        "metric": "ICWF trajectory-steps/s at N=1024",
+        "value": value,
+        "unit": "trajectory-steps/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_s * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": dtype_name,
+        "data": "synthetic (Shin-Metiu potential, BO states and |Psi0|^2 sampling computed here)",
+        "config": {"workload": workload_name(w), "nx": w.nx, "nR": w.nR, "n_traj": w.n_traj,
+                   "dt": w.dt, "rank_k": info["rank"], "svd_rel_cutoff": cutoff,
+                   "svd_tail_rel": info["tail_rel"], "coeff_scheme": "rk4-interpolated",
+                   "obs_every": OBS_EVERY, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if ws > 1 else "single-gpu"},
+        "roofline": rl,
+        "kernels_ms_per_step": {f: v[0] / args.steps for f, v in prof.items() if v[1]},
+        "gpu_launches": int(launches + obs_launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = run_e2e(args, w, params, g)
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = run_cpu_baseline(w, args.cpu_budget_s)
+    return out
+
+
+def run_e2e(args, w, params, g):
+    """The same metric through the public C ABI with host buffers: create (V), projectors,
+    init (Psi0), K steps with observables every 100 steps copied back, destroy."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = g.Icwf(params, w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, w.seed)
+    n_obs = 0
+    done = 0
+    while done < args.steps:
+        k = min(OBS_EVERY, args.steps - done)
+        sim.step(k)
+        done += k
+        if done % OBS_EVERY == 0 or done == args.steps:
+            sim.observables()
+            n_obs += 1
+    sim.close()
+    dt = time.perf_counter() - t0
+    h2d = w.V.nbytes + w.phi.nbytes + w.psi0.nbytes
+    d2h = n_obs * 8 * (w.nx + w.nR + 4 + 64 + 8)
+    return {"value": w.n_traj * args.steps / dt, "unit": "trajectory-steps/s",
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "wall_s": dt, "includes": "create (host SVD of V), init (sampling, slices, C0), steps, "
+                                      "observables copies, destroy"}
+
+
+def run_cpu_baseline(w, budget_s):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the same workload:
+    the first M steps of the same job (M chosen to fit the budget)."""
+    import numpy as np
+    from oracle.icwf import Icwf as Oracle, Params
+    p = Params(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, w.dt,
+               w.n_traj, w.svd_rel_cutoff, w.s_reg_eps)
+    o = Oracle(p, w.V)
+    st = o.init_from_density(w.psi0, w.seed)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(st)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    threads = os.environ.get("OMP_NUM_THREADS")
+    return {"value": w.n_traj * n / dt, "unit": "trajectory-steps/s",
+            "cores": int(threads) if threads else (os.cpu_count() or 1), "kind": "oracle",
+            "sample": f"first {n} steps of the same N={w.n_traj} job (factorised Heff, same rank)",
+            "s_per_step": dt / n}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return None
+    prec, dtype_name, cutoff = MODES[args.mode]
+    w = make_workload(args.n_traj, cutoff)
+    from oracle.icwf import Icwf as Oracle, Params
+    p = Params(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, w.dt,
+               w.n_traj, w.svd_rel_cutoff, w.s_reg_eps)
+    o = Oracle(p, w.V)
+    st = o.init_from_density(w.psi0, w.seed)
+    budget = 150.0
+    t_start = time.perf_counter()
+    for _ in range(args.warmup):
+        o.step(st)
+        if time.perf_counter() - t_start > budget / 3:
+            break
+    t0 = time.perf_counter()
+    n = 0
+    while n < args.steps:
+        o.step(st)
+        n += 1
+        if (n % OBS_EVERY) == 0:
+            o.observables(st, w.phi)
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    value = w.n_traj * n / dt
+    cores = os.cpu_count() or 1
+    return {
+        "impl": "reference", "metric": "ICWF trajectory-steps/s at N=1024", "value": value,
+        "unit": "trajectory-steps/s", "n_gpus": ws, "steps": n, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / n, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "nx": w.nx, "nR": w.nR, "n_traj": w.n_traj,
+                   "dt": w.dt, "rank_k": len(o.fac.s), "svd_rel_cutoff": cutoff},
+        "cpu_baseline": {"value": value, "unit": "trajectory-steps/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{n} of the requested {args.steps} steps (time budget)"},
+        "e2e": {"value": value, "unit": "trajectory-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        out = run_reference(args, rank, ws)
+    else:
+        out = run_ours(args, rank, ws, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

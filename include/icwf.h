@@ -1,0 +1,195 @@
+/*
+ * icwf.h -- C ABI of the GB300 (sm_103a) library for the Interacting Conditional Wavefunction
+ * (ICWF) time step of Albareda, Kelly and Rubio, arXiv 1805.11169.
+ *
+ * The method (paper, Eq. ansatz): the wavefunction of an electron coordinate x and a nuclear or
+ * photon coordinate R is expanded as Psi(x,R,t) = sum_a C_a(t) psi_a(x,t) chi_a(R,t) over N
+ * stochastic trajectories (x_a, R_a).  One time step advances
+ *   - the Bohmian positions with the velocities of Eq. v1/v2,
+ *   - every conditional wavefunction (CWF) under its Hermitian-CWF equation (Eq.
+ *     conditional_e / conditional_n with the complex eta potentials dropped, as the paper
+ *     prescribes for the Hermitian limit), the other coordinate pinned at the trajectory,
+ *   - the coefficients by Eq. coeff, S dC/dt = -i Heff C, with S the overlap (Eq. M) and
+ *     Heff = W - W1 - W2 (Eq. W, W1, W2), pinned at the ket.
+ *
+ * Conventions for every call:
+ *   - All pointers are HOST pointers.  Inputs are copied; the library never keeps caller memory.
+ *     Outputs are written into caller-owned arrays of the documented length.
+ *   - Complex arrays are interleaved (re, im) float64 pairs.
+ *   - Grids are cell-centred and periodic: x_i = x_min + (i + 1/2) dx, dx = (x_max - x_min)/nx.
+ *   - Every call returns an icwf_status; icwf_last_error() gives a one-line description of the
+ *     last failure on that handle (or of the last failed create when called with NULL).
+ *   - Call-order mistakes (step before init, ...) return ICWF_ERR_STATE and change nothing.
+ *   - A non-finite velocity or coefficient, or a failed Cholesky pivot, returns ICWF_ERR_NUMERIC
+ *     (detected when the call's device work ends); the handle's state is then not usable and
+ *     must be re-initialised.
+ *   - Handles are not thread-safe; distinct handles share nothing (except through a pool).
+ *   - All device work of a handle runs on the handle's own CUDA stream on the current device at
+ *     create time; calls return after that work has finished.
+ */
+#ifndef ICWF_H
+#define ICWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct icwf_ctx* icwf_handle;
+typedef struct icwf_pool_ctx* icwf_pool;
+
+typedef enum {
+  ICWF_OK = 0,
+  ICWF_ERR_ARG = 1,      /* invalid argument (size, pointer, range) */
+  ICWF_ERR_STATE = 2,    /* call out of order */
+  ICWF_ERR_OOM = 3,      /* device allocation failed or pool HBM budget exceeded */
+  ICWF_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+  ICWF_ERR_NUMERIC = 5,  /* NaN/Inf in C or S, or Cholesky pivot <= 0 after regularisation */
+  ICWF_ERR_TIMEOUT = 6   /* an in-kernel wait gave up (iteration limit reached) */
+} icwf_status;
+
+typedef enum {
+  ICWF_FP64 = 0,          /* CWFs complex128; matrix elements, solve and RK4 in FP64 */
+  ICWF_MIXED_BF16X3 = 1,  /* CWFs complex64, FP32 propagation; Grams on tcgen05 tensor cores as
+                             three BF16 products (hi*hi + hi*lo + lo*hi), FP32 accumulation;
+                             S regularisation, Cholesky, RK4 and reductions in FP64 */
+  ICWF_MIXED_TF32X3 = 2   /* as above with TF32 operand pieces */
+} icwf_precision;
+
+typedef struct {
+  int32_t nx, nR;           /* grid sizes; powers of two in [8, 4096] (radix-2 FFT) */
+  double x_min, x_max;      /* electron grid extent (periodic cell) */
+  double R_min, R_max;      /* nuclear / photon grid extent */
+  double mass_x, mass_R;    /* masses in atomic units (e.g. 1 and 1836, or 1 and 1) */
+  double dt;                /* time step, a.u. */
+  int32_t n_traj;           /* N >= 1 trajectories (basis functions) */
+  int32_t precision;        /* icwf_precision */
+  double svd_rel_cutoff;    /* rank rule for V_c (see icwf_create); 0 keeps every singular value */
+  double s_reg_eps;         /* Tikhonov shift eps: the solves use S + eps*I (S_aa = 1) */
+  int32_t coeff_scheme;     /* 0: RK4 with S, Heff linear in t over the step (two Cholesky
+                               factorisations per step); 1: S, Heff frozen at t_n (one) */
+  int32_t max_rank;         /* upper bound on the kept rank k (0: no bound beyond the cutoff) */
+} icwf_params;
+
+/* Diagnostic facts about a handle. */
+typedef struct {
+  int32_t rank;             /* kept rank k of the interaction factorisation */
+  double tail_rel;          /* ||dropped part of V_c||_F / ||V_c||_F */
+  double next_rel;          /* first dropped singular value / largest (0 if none dropped) */
+  double sigma_max;         /* largest singular value of V_c */
+  size_t device_bytes;      /* device memory held by the handle */
+  int64_t steps_done;       /* completed time steps since init */
+  double t;                 /* simulated time */
+  int64_t kernel_launches;  /* CUDA kernels launched by icwf_step on this handle since create */
+} icwf_info;
+
+/* Observables of the current state (paper: reduced densities, BO populations and the
+ * decoherence indicator of the Shin-Metiu discussion; norm and energy).  Arrays are
+ * caller-owned; any of them may be NULL to skip it.
+ *   rho_x[nx]  = int dR |Psi(x_i, R)|^2        rho_R[nR] = int dx |Psi(x, R_j)|^2
+ *   pop[n_s]   = int dR |chi^(n)(R)|^2,        chi^(n)(R) = int dx phi_n(x; R) Psi(x, R)
+ *   decoh[n_s*n_s] = int dR |chi^(n)|^2 |chi^(m)|^2   (row-major n, m)
+ *   norm = <Psi|Psi>,  energy = <Psi|T_x + T_R + V|Psi> / <Psi|Psi>.
+ * pop and decoh need icwf_set_projectors; otherwise they are left untouched. */
+typedef struct {
+  double t;
+  double norm;
+  double energy;
+  double* rho_x;
+  double* rho_R;
+  double* pop;
+  double* decoh;
+  int32_t n_states;         /* out: number of projectors set (0 if none) */
+  int32_t n_clamped;        /* out: cumulative count of positions clamped to the grid */
+} icwf_obs;
+
+/* Create a handle for the problem of the paper's Eq. TDSE with 1D x and R and no vector
+ * potential: grids, masses, dt and N from *p; V[i*nR + j] = V(x_i, R_j) (float64, host,
+ * copied).  Double-centres V = v1(x) + v2(R) + V_c and keeps the smallest rank k of the SVD of
+ * V_c whose Frobenius tail is <= svd_rel_cutoff * ||V_c||_F (the factorisation used for the
+ * matrix elements of Eq. W, which the paper flags as costly for large ensembles).
+ * Allocates every device buffer.  On failure *out is NULL and icwf_last_error(NULL) explains. */
+icwf_status icwf_create(const icwf_params* p, const double* V, icwf_handle* out);
+
+/* Real BO states used as population projectors: phi[(n*nR + j)*nx + i] = phi_n(x_i; R_j),
+ * n < n_states <= 8 (host, copied).  Optional; may be called at any time after create. */
+icwf_status icwf_set_projectors(icwf_handle h, int32_t n_states, const double* phi);
+
+/* Initialise from Psi0: psi0[2*(i*nR + j) + {0,1}] = Psi0(x_i, R_j) (complex128, host, copied).
+ * Samples N positions from |Psi0|^2 with SplitMix64(seed) (cell by inverse CDF over the
+ * row-major flattened density, then uniform jitter inside the cell), slices the CWFs
+ * psi_a = Psi0(., R_a), chi_a = Psi0(x_a, .) by 4-point cubic Lagrange interpolation along the
+ * other axis (Eq. CWF1/CWF2), normalises each to 1, assembles S_0 and Heff_0 and sets
+ * C_0 = (S_0 + eps I)^-1 <phi_a|Psi0>.  Resets t and the step counter. */
+icwf_status icwf_init_from_density(icwf_handle h, const double* psi0, uint64_t seed);
+
+/* As icwf_init_from_density with caller-chosen positions x[N], R[N] (no sampling). */
+icwf_status icwf_init_from_positions(icwf_handle h, const double* psi0, const double* x,
+                                     const double* R);
+
+/* Advance n_steps >= 0 time steps (velocities, positions, CWF propagation, matrices at
+ * t + dt, coefficients).  Returns when the device has finished. */
+icwf_status icwf_step(icwf_handle h, int32_t n_steps);
+
+/* Compute observables of the current state into *out (see icwf_obs). */
+icwf_status icwf_observables(icwf_handle h, icwf_obs* out);
+
+/* Release the handle and all its device memory.  NULL is a no-op. */
+icwf_status icwf_destroy(icwf_handle h);
+
+/* --- diagnostics and tests ---------------------------------------------------------------- */
+
+/* Copy the state out.  C[2N], x[N], R[N] float64; psi[2*nx*N], chi[2*nR*N] complex128 with
+ * psi[2*(a*nx + i)] = Re psi_a(x_i) (column a contiguous).  Any pointer may be NULL. */
+icwf_status icwf_get_state(icwf_handle h, double* C, double* x, double* R, double* psi,
+                           double* chi);
+
+/* Copy the N x N matrices at the current time, row-major complex128 [2*(a*N + b)]:
+ * S (Eq. M), H = <phi_a|T_x + T_R + V|phi_b> and Heff = W - W1 - W2.  Any pointer may be NULL;
+ * H costs extra Grams and is computed only when requested. */
+icwf_status icwf_get_matrices(icwf_handle h, double* S, double* H, double* Heff);
+
+icwf_status icwf_get_info(icwf_handle h, icwf_info* out);
+
+/* The handle's CUDA stream (a cudaStream_t) for callers that record events on it. */
+icwf_status icwf_get_stream(icwf_handle h, void** stream);
+
+/* Per-kernel device timing.  While enabled, every kernel launch of icwf_step is bracketed by
+ * CUDA events on the handle's stream and its duration accumulated per kernel family.
+ * icwf_profile_read fills up to n entries: names (static strings), total ms and launch
+ * counts; it returns the number of families in *n_out. */
+icwf_status icwf_profile_enable(icwf_handle h, int32_t on);
+icwf_status icwf_profile_reset(icwf_handle h);
+icwf_status icwf_profile_read(icwf_handle h, int32_t n, const char** names, double* ms,
+                              int64_t* launches, int32_t* n_out);
+
+/* Text of the last failure on h (or of the last failed icwf_create / pool call if h is NULL). */
+const char* icwf_last_error(icwf_handle h);
+
+/* --- serving pool: continuous batching of independent jobs -------------------------------- */
+
+/* A pool admits jobs while their summed device footprint stays within hbm_budget_bytes and at
+ * most max_jobs are live; pending jobs wait in arrival order.  Every icwf_pool_tick advances
+ * every live job by one step, the jobs' kernels grouped per kernel family. */
+icwf_status icwf_pool_create(size_t hbm_budget_bytes, int32_t max_jobs, icwf_pool* out);
+
+/* Hand an initialised job to the pool (the pool owns it from now on) to run n_steps steps.
+ * *job_id identifies it in icwf_pool_poll. */
+icwf_status icwf_pool_submit(icwf_pool pool, icwf_handle job, int64_t n_steps, int32_t* job_id);
+
+/* One step of every live job; admits pending jobs first. *n_live and *n_finished (may be NULL)
+ * report the live count after the tick and the jobs that finished in it. */
+icwf_status icwf_pool_tick(icwf_pool pool, int32_t* n_live, int32_t* n_finished);
+
+/* *state: 0 pending, 1 live, 2 finished, 3 failed.  When finished, fills *out (if not NULL)
+ * with the job's final observables and releases its device memory. */
+icwf_status icwf_pool_poll(icwf_pool pool, int32_t job_id, icwf_obs* out, int32_t* state);
+
+icwf_status icwf_pool_destroy(icwf_pool pool);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICWF_H */

@@ -1,0 +1,1060 @@
+// Host side of the C ABI declared in include/icwf.h: handle life cycle, the rank-k factorisation
+// of the interaction, the seeded sampler, initialisation, the per-step kernel schedule,
+// observables, diagnostics, per-kernel timing and the serving pool.
+//
+// Compiled with -ffp-contract=off so that the sampler and the grid formulas round exactly as
+// written (the sampler must reproduce the published SplitMix64 stream and the inverse-CDF draw
+// bit for bit on every host architecture).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "icwf_internal.h"
+
+namespace icwf {
+void jacobi_svd(int m, int n, std::vector<double>& A, std::vector<double>& s,
+                std::vector<double>& U, std::vector<double>& Vr);
+}
+
+using namespace icwf;
+
+namespace {
+
+thread_local std::string g_err;   // last failure without a handle
+
+enum Fam {
+  F_VELOCITY, F_PROPAGATE, F_ASSEMBLE, F_SHIFT, F_POTRF, F_MATVEC, F_SOLVE, F_RK4, F_OBS,
+  F_COUNT
+};
+const char* kFamNames[F_COUNT] = {"velocity", "propagate", "assemble", "shift",
+                                  "cholesky", "rk4_matvec", "chol_solve", "rk4_final",
+                                  "observables"};
+
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  void* take(size_t bytes) {
+    const size_t off = (used + 255) & ~(size_t)255;
+    if (off + bytes > size) return nullptr;
+    used = off + bytes;
+    return base + off;
+  }
+};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct icwf_ctx {
+  icwf_params p{};
+  std::string err;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool mixed = false;
+  int N = 0, nx = 0, nR = 0, K = 0, logx = 0, logR = 0;
+  double dx = 0, dR = 0;
+  double tail_rel = 0, next_rel = 0, sigma_max = 0;
+  size_t cwf_elem = 16;   // bytes per complex CWF sample
+  // device memory
+  Arena arena;
+  double *V = nullptr, *U = nullptr, *W = nullptr, *sig = nullptr, *v1 = nullptr, *v2 = nullptr;
+  void* Vt = nullptr;
+  void *kinx = nullptr, *kinR = nullptr, *twx = nullptr, *twR = nullptr;
+  double2 *twx_d = nullptr, *twR_d = nullptr;
+  void *psi = nullptr, *chi = nullptr;
+  double *x = nullptr, *R = nullptr, *xo = nullptr, *Ro = nullptr;
+  double *px = nullptr, *pR = nullptr, *dvec = nullptr;
+  double2* C = nullptr;
+  double2* kk[4] = {nullptr, nullptr, nullptr, nullptr};
+  double2 *y = nullptr, *work = nullptr;
+  double2 *S[2] = {nullptr, nullptr}, *H[2] = {nullptr, nullptr};
+  double2 *L[2] = {nullptr, nullptr}, *Lh = nullptr;
+  unsigned *flags = nullptr, *tickets = nullptr;
+  int* status = nullptr;
+  int cur = 0;
+  unsigned epoch = 0;
+  // observables (allocated on first use)
+  double2* Psi = nullptr;
+  double* phi = nullptr;
+  int n_states = 0;
+  double *rho_x = nullptr, *rho_R = nullptr, *part = nullptr, *obs_out = nullptr;
+  double *pop = nullptr, *decoh = nullptr;
+  double2* proj = nullptr;
+  std::vector<void*> extra_allocs;
+  // tensor-core assembly scratch
+  void* tc_scratch = nullptr;
+  size_t tc_scratch_bytes = 0;
+  // state
+  bool initialised = false;
+  int64_t steps = 0;
+  double t = 0.0;
+  int64_t launches = 0;   // kernels launched by icwf_step
+  // profiling
+  bool prof_on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double prof_ms[F_COUNT] = {0};
+  int64_t prof_n[F_COUNT] = {0};
+};
+
+namespace {
+
+icwf_status fail(icwf_ctx* h, icwf_status st, const std::string& msg) {
+  if (h) h->err = msg; else g_err = msg;
+  return st;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, ICWF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+JobView view(icwf_ctx* h) {
+  JobView j;
+  j.N = h->N; j.nx = h->nx; j.nR = h->nR; j.K = h->K; j.logx = h->logx; j.logR = h->logR;
+  j.x_min = h->p.x_min; j.dx = h->dx; j.R_min = h->p.R_min; j.dR = h->dR;
+  j.inv_mx = 1.0 / h->p.mass_x; j.inv_mR = 1.0 / h->p.mass_R; j.dt = h->p.dt;
+  j.eps = h->p.s_reg_eps;
+  j.V = h->V; j.Vt = h->Vt; j.U = h->U; j.W = h->W; j.sig = h->sig; j.v1 = h->v1; j.v2 = h->v2;
+  j.psi = h->psi; j.chi = h->chi;
+  j.x = h->x; j.R = h->R; j.xo = h->xo; j.Ro = h->Ro;
+  j.px = h->px; j.pR = h->pR; j.d = h->dvec;
+  j.kinx = h->kinx; j.kinR = h->kinR; j.twx = h->twx; j.twR = h->twR;
+  j.status = h->status;
+  return j;
+}
+
+// ---- per-kernel timing -----------------------------------------------------------------------
+
+cudaEvent_t take_event(icwf_ctx* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  icwf_ctx* h;
+  int fam;
+  cudaEvent_t a = nullptr;
+  ProfScope(icwf_ctx* h_, int f) : h(h_), fam(f) {
+    if (h->prof_on) {
+      a = take_event(h);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~ProfScope() {
+    if (h->prof_on) {
+      cudaEvent_t b = take_event(h);
+      cudaEventRecord(b, h->stream);
+      h->pending.push_back({fam, {a, b}});
+    }
+  }
+};
+
+void prof_collect(icwf_ctx* h) {
+  for (auto& pe : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      h->prof_ms[pe.first] += ms;
+      h->prof_n[pe.first] += 1;
+    }
+    h->event_pool.push_back(pe.second.first);
+    h->event_pool.push_back(pe.second.second);
+  }
+  h->pending.clear();
+}
+
+// ---- host numerics --------------------------------------------------------------------------
+
+struct HStencil { int i0; double w[4]; };
+
+// Same stencil as the device one (4-point cubic Lagrange, start clamped to [0, n-4]).
+HStencil h_lagrange4(double p, double lo, double d, int n) {
+  HStencil st;
+  const double s = (p - lo) / d - 0.5;
+  int i0 = (int)std::floor(s) - 1;
+  i0 = i0 < 0 ? 0 : (i0 > n - 4 ? n - 4 : i0);
+  const double u = s - (double)i0;
+  const double u1 = u - 1.0, u2 = u - 2.0, u3 = u - 3.0;
+  st.i0 = i0;
+  st.w[0] = -(u1 * u2 * u3) / 6.0;
+  st.w[1] = (u * u2 * u3) / 2.0;
+  st.w[2] = -(u * u1 * u3) / 2.0;
+  st.w[3] = (u * u1 * u2) / 6.0;
+  return st;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): state += golden gamma; Stafford variant-13 finaliser.
+struct SplitMix64 {
+  uint64_t s;
+  explicit SplitMix64(uint64_t seed) : s(seed) {}
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+// Bit-reversed kinetic phase exp(-i k^2 dt / 2m) / n and twiddles exp(-2 pi i k / n).
+void kinetic_tables(int n, double d, double mass, double dt, std::vector<double>& kin,
+                    std::vector<double>& tw) {
+  const int logn = ilog2(n);
+  const double PI = 3.14159265358979323846;
+  kin.resize(2 * (size_t)n);
+  tw.resize(n);   // n/2 complex
+  for (int mp = 0; mp < n; ++mp) {
+    int m = 0;
+    for (int b = 0; b < logn; ++b) if (mp & (1 << b)) m |= 1 << (logn - 1 - b);
+    const int mm = m < n / 2 ? m : m - n;
+    const double k = 2.0 * PI * (double)mm / ((double)n * d);
+    const double ph = -k * k * dt / (2.0 * mass);
+    kin[2 * mp] = std::cos(ph) / n;
+    kin[2 * mp + 1] = std::sin(ph) / n;
+  }
+  for (int k = 0; k < n / 2; ++k) {
+    const double a = -2.0 * PI * (double)k / (double)n;
+    tw[2 * k] = std::cos(a);
+    tw[2 * k + 1] = std::sin(a);
+  }
+}
+
+template <typename T>
+std::vector<T> cast_vec(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+icwf_status upload(icwf_ctx* h, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
+  return ICWF_OK;
+}
+
+icwf_status sync_status(icwf_ctx* h, const char* where) {
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->prof_on) prof_collect(h);
+  int st[2];
+  CK(cudaMemcpy(st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0] & ST_TIMEOUT) return fail(h, ICWF_ERR_TIMEOUT, std::string(where) + ": in-kernel wait timed out");
+  if (st[0] & (ST_NONFINITE | ST_CHOL)) {
+    return fail(h, ICWF_ERR_NUMERIC,
+                std::string(where) + ((st[0] & ST_CHOL) ? ": Cholesky pivot <= 0 (S + eps I not positive definite)"
+                                                        : ": non-finite velocity or coefficient"));
+  }
+  return ICWF_OK;
+}
+
+// Factor L[dst] = chol(S_src + eps I) (theta selects the mix of S[cur] and S[nxt]).
+void factor(icwf_ctx* h, const double2* S0, const double2* S1, double theta, double2* dst) {
+  {
+    ProfScope ps(h, F_SHIFT);
+    launch_shift_mix(h->N, S0, S1, h->p.s_reg_eps, theta, dst, h->stream);
+  }
+  ProfScope ps(h, F_POTRF);
+  double2* arr[2] = {dst, dst};
+  launch_cholesky(h->N, arr, 1, h->status, h->stream);
+  const int T = (h->N + 31) / 32;
+  h->launches += 1 + (3 * T - 2);   // shift + potrf/trsm/herk per panel
+}
+
+void solve(icwf_ctx* h, const double2* Lf, const double2* y, double2* out, bool minus_i) {
+  ProfScope ps(h, F_SOLVE);
+  ++h->epoch;
+  launch_chol_solve(h->N, Lf, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
+                    h->status, h->stream);
+  h->launches += 2;
+}
+
+void assemble(icwf_ctx* h, double2* S, double2* Hm) {
+  ProfScope ps(h, F_ASSEMBLE);
+  h->launches += 1;
+  JobView j = view(h);
+  if (h->mixed) {
+    launch_assemble_tc(j, h->p.precision, S, Hm, h->tc_scratch, h->tc_scratch_bytes, h->stream);
+  } else {
+    launch_assemble_fp64(j, S, Hm, h->stream);
+  }
+}
+
+// One ICWF step t_n -> t_{n+1}.
+void step_once(icwf_ctx* h) {
+  JobView j = view(h);
+  const int cur = h->cur, nxt = 1 - cur;
+  const double dt = h->p.dt;
+  {
+    ProfScope ps(h, F_VELOCITY);
+    if (h->mixed) launch_velocity<float>(j, h->C, h->stream);
+    else launch_velocity<double>(j, h->C, h->stream);
+    h->launches += 1;
+  }
+  {
+    ProfScope ps(h, F_PROPAGATE);
+    if (h->mixed) launch_propagate<float>(j, h->stream);
+    else launch_propagate<double>(j, h->stream);
+    h->launches += 1;
+  }
+  assemble(h, h->S[nxt], h->H[nxt]);
+  double2 *Lc = h->L[cur], *Ln = h->L[nxt];
+  if (h->p.coeff_scheme == 1) {
+    // S, Heff frozen at t_n over the step: every stage uses L[cur], H[cur]
+    for (int st = 0; st < 4; ++st) {
+      const double c = st == 0 ? 0.0 : (st == 3 ? dt : 0.5 * dt);
+      {
+        ProfScope ps(h, F_MATVEC);
+        launch_matvec(h->N, h->H[cur], h->H[cur], 0.0, h->C, st ? h->kk[st - 1] : nullptr, c, h->y,
+                      h->stream);
+        h->launches += 1;
+      }
+      solve(h, Lc, h->y, h->kk[st], true);
+    }
+    factor(h, h->S[nxt], h->S[nxt], 1.0, Ln);
+  } else {
+    factor(h, h->S[cur], h->S[nxt], 0.5, h->Lh);
+    factor(h, h->S[nxt], h->S[nxt], 1.0, Ln);
+    const double thetas[4] = {0.0, 0.5, 0.5, 1.0};
+    const double2* Ls[4] = {Lc, h->Lh, h->Lh, Ln};
+    for (int st = 0; st < 4; ++st) {
+      const double c = st == 0 ? 0.0 : (st == 3 ? dt : 0.5 * dt);
+      {
+        ProfScope ps(h, F_MATVEC);
+        launch_matvec(h->N, h->H[cur], h->H[nxt], thetas[st], h->C, st ? h->kk[st - 1] : nullptr,
+                      c, h->y, h->stream);
+        h->launches += 1;
+      }
+      solve(h, Ls[st], h->y, h->kk[st], true);
+    }
+  }
+  {
+    ProfScope ps(h, F_RK4);
+    launch_rk4_final(h->N, h->C, h->kk[0], h->kk[1], h->kk[2], h->kk[3], dt, h->status,
+                     h->stream);
+    h->launches += 1;
+  }
+  h->cur = nxt;
+  h->steps += 1;
+  h->t += dt;
+}
+
+icwf_status alloc_obs(icwf_ctx* h) {
+  if (h->Psi) return ICWF_OK;
+  void* p = nullptr;
+  const size_t bytes = align256((size_t)h->nx * h->nR * sizeof(double2)) +
+                       align256((size_t)(h->nx + h->nR) * sizeof(double)) * 2 +
+                       align256((size_t)(2 * h->nR + h->nx) * sizeof(double)) + align256(64 * sizeof(double)) +
+                       align256(8 * sizeof(double)) + align256(64 * sizeof(double)) +
+                       align256((size_t)8 * h->nR * sizeof(double2));
+  CK(cudaMalloc(&p, bytes));
+  h->extra_allocs.push_back(p);
+  Arena a{(char*)p, bytes, 0};
+  h->Psi = (double2*)a.take((size_t)h->nx * h->nR * sizeof(double2));
+  h->rho_x = (double*)a.take((size_t)(h->nx + h->nR) * sizeof(double));
+  h->rho_R = (double*)a.take((size_t)(h->nx + h->nR) * sizeof(double));
+  h->part = (double*)a.take((size_t)(2 * h->nR + h->nx) * sizeof(double));
+  h->obs_out = (double*)a.take(64 * sizeof(double));
+  h->pop = (double*)a.take(8 * sizeof(double));
+  h->decoh = (double*)a.take(64 * sizeof(double));
+  h->proj = (double2*)a.take((size_t)8 * h->nR * sizeof(double2));
+  return ICWF_OK;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+
+extern "C" {
+
+const char* icwf_last_error(icwf_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* out) {
+  icwf_ctx* h = nullptr;
+  if (!out) return fail(nullptr, ICWF_ERR_ARG, "icwf_create: out is NULL");
+  *out = nullptr;
+  if (!pp || !Vh) return fail(nullptr, ICWF_ERR_ARG, "icwf_create: params or V is NULL");
+  const icwf_params& p = *pp;
+  if (!pow2(p.nx) || !pow2(p.nR) || p.nx < 8 || p.nR < 8 || p.nx > 4096 || p.nR > 4096)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: nx and nR must be powers of two in [8, 4096]");
+  if (p.n_traj < 1 || p.n_traj > 16384)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: n_traj must be in [1, 16384]");
+  if (!(p.x_max > p.x_min) || !(p.R_max > p.R_min) || !(p.mass_x > 0) || !(p.mass_R > 0) ||
+      !(p.dt > 0) || !(p.s_reg_eps >= 0) || !(p.svd_rel_cutoff >= 0))
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: invalid extents, masses, dt, eps or cutoff");
+  if (p.precision < 0 || p.precision > 2)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: unknown precision");
+  if (p.precision != ICWF_FP64 && assemble_tc_scratch_bytes(p.n_traj, p.nx, p.nR, 1) == 0)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: mixed precision is not available in this build");
+  if (p.coeff_scheme < 0 || p.coeff_scheme > 1)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: unknown coeff_scheme");
+  const size_t nV = (size_t)p.nx * p.nR;
+  for (size_t e = 0; e < nV; ++e)
+    if (!std::isfinite(Vh[e])) return fail(nullptr, ICWF_ERR_ARG, "icwf_create: V has a non-finite entry");
+
+  std::unique_ptr<icwf_ctx> hp(new icwf_ctx);
+  h = hp.get();
+  h->p = p;
+  h->N = p.n_traj; h->nx = p.nx; h->nR = p.nR;
+  h->logx = ilog2(p.nx); h->logR = ilog2(p.nR);
+  h->dx = (p.x_max - p.x_min) / p.nx;
+  h->dR = (p.R_max - p.R_min) / p.nR;
+  h->mixed = p.precision != ICWF_FP64;
+  h->cwf_elem = h->mixed ? sizeof(float2) : sizeof(double2);
+  cudaGetDevice(&h->device);
+
+  // ---- double-centring and SVD of the interaction (host, FP64) ----
+  const int nx = p.nx, nR = p.nR;
+  std::vector<double> v1(nx, 0.0), v2(nR, 0.0);
+  double grand = 0.0;
+  for (int i = 0; i < nx; ++i) {
+    double s = 0.0;
+    for (int jj = 0; jj < nR; ++jj) s += Vh[(size_t)i * nR + jj];
+    v1[i] = s / nR;
+  }
+  for (int jj = 0; jj < nR; ++jj) {
+    double s = 0.0;
+    for (int i = 0; i < nx; ++i) s += Vh[(size_t)i * nR + jj];
+    v2[jj] = s / nx;
+  }
+  for (int i = 0; i < nx; ++i) grand += v1[i];
+  grand /= nx;
+  for (int jj = 0; jj < nR; ++jj) v2[jj] -= grand;
+  // V_c column-major in the longer dimension so that m >= n
+  const bool tr = nx < nR;
+  const int m = tr ? nR : nx, n = tr ? nx : nR;
+  std::vector<double> A((size_t)m * n);
+  double fro2 = 0.0;
+  for (int i = 0; i < nx; ++i)
+    for (int jj = 0; jj < nR; ++jj) {
+      const double vc = Vh[(size_t)i * nR + jj] - v1[i] - v2[jj];
+      fro2 += vc * vc;
+      if (!tr) A[(size_t)jj * nx + i] = vc; else A[(size_t)i * nR + jj] = vc;
+    }
+  std::vector<double> s, Um, Vr;
+  jacobi_svd(m, n, A, s, Um, Vr);
+  int K = n;
+  double tail2 = 0.0;
+  {
+    // smallest k whose Frobenius tail is within the cutoff
+    std::vector<double> tails(n + 1, 0.0);
+    for (int k = n - 1; k >= 0; --k) tails[k] = tails[k + 1] + s[k] * s[k];
+    const double fro = std::sqrt(tails[0]);
+    if (p.svd_rel_cutoff > 0 && fro > 0) {
+      K = n;
+      for (int k = 0; k < n; ++k)
+        if (std::sqrt(tails[k]) <= p.svd_rel_cutoff * fro) { K = k; break; }
+    }
+    if (p.max_rank > 0 && K > p.max_rank) K = p.max_rank;
+    tail2 = tails[K];
+    h->tail_rel = fro > 0 ? std::sqrt(tail2) / fro : 0.0;
+    h->next_rel = (K < n && s[0] > 0) ? s[K] / s[0] : 0.0;
+    h->sigma_max = n > 0 ? s[0] : 0.0;
+  }
+  if (K < 1) K = 1;   // keep one (possibly zero) term so that the kernels see K >= 1
+  h->K = K;
+  std::vector<double> Uk((size_t)K * nx), Wk((size_t)K * nR), sk(K);
+  for (int k = 0; k < K; ++k) {
+    sk[k] = k < n ? s[k] : 0.0;
+    for (int i = 0; i < nx; ++i) Uk[(size_t)k * nx + i] = tr ? Vr[(size_t)k * n + i] : Um[(size_t)k * m + i];
+    for (int jj = 0; jj < nR; ++jj) Wk[(size_t)k * nR + jj] = tr ? Um[(size_t)k * m + jj] : Vr[(size_t)k * n + jj];
+  }
+
+  // ---- device memory ----
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(nullptr, ICWF_ERR_CUDA, "icwf_create: cudaStreamCreate failed");
+  const int N = h->N;
+  const size_t cw = h->cwf_elem, rw = h->mixed ? sizeof(float) : sizeof(double);
+  const size_t NN = (size_t)N * N;
+  const int nblk = (N + 31) / 32;
+  std::vector<size_t> sizes = {
+      nV * sizeof(double), nV * rw, (size_t)K * nx * 8, (size_t)K * nR * 8, (size_t)K * 8,
+      (size_t)nx * 8, (size_t)nR * 8,
+      (size_t)nx * cw, (size_t)nR * cw, (size_t)nx / 2 * cw, (size_t)nR / 2 * cw,
+      (size_t)nx / 2 * 16, (size_t)nR / 2 * 16,
+      (size_t)N * nx * cw, (size_t)N * nR * cw,
+      (size_t)N * 8 * 4, (size_t)K * N * 8 * 2, (size_t)N * 8,
+      (size_t)N * 16 * 8,  // C, k1..k4, y, work(2N)
+      NN * 16 * 7,         // S[2], H[2], L[2], Lh
+      (size_t)2 * nblk * 4 + 64, 64 * 4};
+  size_t total = 0;
+  for (size_t b : sizes) total += align256(b);
+  if (h->mixed) {
+    h->tc_scratch_bytes = assemble_tc_scratch_bytes(N, nx, nR, K);
+    total += align256(h->tc_scratch_bytes);
+  }
+  total += 4096;
+  if (cudaMalloc(&h->arena.base, total) != cudaSuccess) {
+    cudaStreamDestroy(h->stream);
+    return fail(nullptr, ICWF_ERR_OOM, "icwf_create: cudaMalloc of " + std::to_string(total) + " bytes failed");
+  }
+  h->arena.size = total;
+  Arena& a = h->arena;
+  h->V = (double*)a.take(nV * 8);
+  h->Vt = a.take(nV * rw);
+  h->U = (double*)a.take((size_t)K * nx * 8);
+  h->W = (double*)a.take((size_t)K * nR * 8);
+  h->sig = (double*)a.take((size_t)K * 8);
+  h->v1 = (double*)a.take((size_t)nx * 8);
+  h->v2 = (double*)a.take((size_t)nR * 8);
+  h->kinx = a.take((size_t)nx * cw);
+  h->kinR = a.take((size_t)nR * cw);
+  h->twx = a.take((size_t)nx / 2 * cw);
+  h->twR = a.take((size_t)nR / 2 * cw);
+  h->twx_d = (double2*)a.take((size_t)nx / 2 * 16);
+  h->twR_d = (double2*)a.take((size_t)nR / 2 * 16);
+  h->psi = a.take((size_t)N * nx * cw);
+  h->chi = a.take((size_t)N * nR * cw);
+  h->x = (double*)a.take((size_t)N * 8);
+  h->R = (double*)a.take((size_t)N * 8);
+  h->xo = (double*)a.take((size_t)N * 8);
+  h->Ro = (double*)a.take((size_t)N * 8);
+  h->px = (double*)a.take((size_t)K * N * 8);
+  h->pR = (double*)a.take((size_t)K * N * 8);
+  h->dvec = (double*)a.take((size_t)N * 8);
+  h->C = (double2*)a.take((size_t)N * 16);
+  for (int q = 0; q < 4; ++q) h->kk[q] = (double2*)a.take((size_t)N * 16);
+  h->y = (double2*)a.take((size_t)N * 16);
+  h->work = (double2*)a.take((size_t)2 * N * 16);
+  for (int q = 0; q < 2; ++q) {
+    h->S[q] = (double2*)a.take(NN * 16);
+    h->H[q] = (double2*)a.take(NN * 16);
+    h->L[q] = (double2*)a.take(NN * 16);
+  }
+  h->Lh = (double2*)a.take(NN * 16);
+  h->flags = (unsigned*)a.take((size_t)2 * nblk * 4 + 64);
+  h->tickets = h->flags + 2 * nblk;
+  h->status = (int*)a.take(64 * 4);
+  if (h->mixed) h->tc_scratch = a.take(h->tc_scratch_bytes);
+  if (!h->status || (h->mixed && !h->tc_scratch)) {
+    cudaFree(h->arena.base);
+    cudaStreamDestroy(h->stream);
+    return fail(nullptr, ICWF_ERR_OOM, "icwf_create: arena layout overflow");
+  }
+
+  // ---- tables ----
+  std::vector<double> kx, twx, kR, twR;
+  kinetic_tables(nx, h->dx, p.mass_x, p.dt, kx, twx);
+  kinetic_tables(nR, h->dR, p.mass_R, p.dt, kR, twR);
+  icwf_status st;
+#define UP(dst, src, bytes) do { st = upload(h, dst, src, bytes); if (st) { g_err = h->err; cudaFree(h->arena.base); cudaStreamDestroy(h->stream); return st; } } while (0)
+  UP(h->V, Vh, nV * 8);
+  std::vector<float> Vf, kxf, kRf, twxf, twRf;
+  if (h->mixed) {
+    Vf.assign(Vh, Vh + nV);
+    kxf = cast_vec<float>(kx); kRf = cast_vec<float>(kR);
+    twxf = cast_vec<float>(twx); twRf = cast_vec<float>(twR);
+    UP(h->Vt, Vf.data(), nV * 4);
+    UP(h->kinx, kxf.data(), kxf.size() * 4);
+    UP(h->kinR, kRf.data(), kRf.size() * 4);
+    UP(h->twx, twxf.data(), twxf.size() * 4);
+    UP(h->twR, twRf.data(), twRf.size() * 4);
+  } else {
+    UP(h->Vt, Vh, nV * 8);
+    UP(h->kinx, kx.data(), kx.size() * 8);
+    UP(h->kinR, kR.data(), kR.size() * 8);
+    UP(h->twx, twx.data(), twx.size() * 8);
+    UP(h->twR, twR.data(), twR.size() * 8);
+  }
+  UP(h->twx_d, twx.data(), twx.size() * 8);
+  UP(h->twR_d, twR.data(), twR.size() * 8);
+  UP(h->U, Uk.data(), Uk.size() * 8);
+  UP(h->W, Wk.data(), Wk.size() * 8);
+  UP(h->sig, sk.data(), sk.size() * 8);
+  UP(h->v1, v1.data(), v1.size() * 8);
+  UP(h->v2, v2.data(), v2.size() * 8);
+#undef UP
+  if (cudaMemsetAsync(h->flags, 0, (size_t)2 * nblk * 4 + 64, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->status, 0, 64 * 4, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaFree(h->arena.base);
+    cudaStreamDestroy(h->stream);
+    return fail(nullptr, ICWF_ERR_CUDA, "icwf_create: initial device transfer failed");
+  }
+  *out = hp.release();
+  return ICWF_OK;
+}
+
+icwf_status icwf_destroy(icwf_handle h) {
+  if (!h) return ICWF_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& pe : h->pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (auto e : h->event_pool) cudaEventDestroy(e);
+  for (void* p : h->extra_allocs) cudaFree(p);
+  if (h->phi) cudaFree(h->phi);
+  if (h->arena.base) cudaFree(h->arena.base);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return ICWF_OK;
+}
+
+icwf_status icwf_set_projectors(icwf_handle h, int32_t n_states, const double* phi) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_set_projectors: NULL handle");
+  if (n_states < 0 || n_states > 8 || (n_states > 0 && !phi))
+    return fail(h, ICWF_ERR_ARG, "icwf_set_projectors: n_states must be in [0, 8] with phi given");
+  if (h->phi) { cudaFree(h->phi); h->phi = nullptr; }
+  h->n_states = 0;
+  if (n_states == 0) return ICWF_OK;
+  const size_t bytes = (size_t)n_states * h->nR * h->nx * sizeof(double);
+  CK(cudaMalloc(&h->phi, bytes));
+  CK(cudaMemcpy(h->phi, phi, bytes, cudaMemcpyHostToDevice));
+  h->n_states = n_states;
+  return ICWF_OK;
+}
+
+static icwf_status init_common(icwf_handle h, const double* psi0, const std::vector<double>& xs,
+                               const std::vector<double>& Rs) {
+  const int N = h->N, nx = h->nx, nR = h->nR;
+  for (int a = 0; a < N; ++a)
+    if (!std::isfinite(xs[a]) || !std::isfinite(Rs[a]))
+      return fail(h, ICWF_ERR_ARG, "init: non-finite position");
+  // slices Psi0(., R_a) and Psi0(x_a, .) by cubic Lagrange interpolation, normalised
+  std::vector<double> ps((size_t)2 * N * nx), cs((size_t)2 * N * nR);
+  for (int a = 0; a < N; ++a) {
+    const HStencil sR = h_lagrange4(Rs[a], h->p.R_min, h->dR, nR);
+    double nrm = 0.0;
+    for (int i = 0; i < nx; ++i) {
+      double re = 0.0, im = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const size_t e = 2 * ((size_t)i * nR + sR.i0 + q);
+        re += sR.w[q] * psi0[e];
+        im += sR.w[q] * psi0[e + 1];
+      }
+      ps[2 * ((size_t)a * nx + i)] = re;
+      ps[2 * ((size_t)a * nx + i) + 1] = im;
+      nrm += re * re + im * im;
+    }
+    nrm = std::sqrt(h->dx * nrm);
+    if (!(nrm > 0)) return fail(h, ICWF_ERR_ARG, "init: Psi0 vanishes along a trajectory's slice");
+    for (int i = 0; i < 2 * nx; ++i) ps[(size_t)2 * a * nx + i] /= nrm;
+    const HStencil sx = h_lagrange4(xs[a], h->p.x_min, h->dx, nx);
+    nrm = 0.0;
+    for (int jj = 0; jj < nR; ++jj) {
+      double re = 0.0, im = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const size_t e = 2 * ((size_t)(sx.i0 + q) * nR + jj);
+        re += sx.w[q] * psi0[e];
+        im += sx.w[q] * psi0[e + 1];
+      }
+      cs[2 * ((size_t)a * nR + jj)] = re;
+      cs[2 * ((size_t)a * nR + jj) + 1] = im;
+      nrm += re * re + im * im;
+    }
+    nrm = std::sqrt(h->dR * nrm);
+    if (!(nrm > 0)) return fail(h, ICWF_ERR_ARG, "init: Psi0 vanishes along a trajectory's slice");
+    for (int jj = 0; jj < 2 * nR; ++jj) cs[(size_t)2 * a * nR + jj] /= nrm;
+  }
+  // FP64 scratch for the projection b_a = <phi_a|Psi0>
+  void* tmp = nullptr;
+  const size_t b_psi = (size_t)N * nx * 16, b_chi = (size_t)N * nR * 16, b_p0 = (size_t)nx * nR * 16;
+  CK(cudaMalloc(&tmp, align256(b_psi) + align256(b_chi) + align256(b_p0) + 256));
+  Arena a{(char*)tmp, align256(b_psi) + align256(b_chi) + align256(b_p0) + 256, 0};
+  double2* dpsi = (double2*)a.take(b_psi);
+  double2* dchi = (double2*)a.take(b_chi);
+  double2* dp0 = (double2*)a.take(b_p0);
+  icwf_status st = ICWF_OK;
+  auto cleanup = [&]() { cudaStreamSynchronize(h->stream); cudaFree(tmp); };
+#define CKI(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cleanup(); return fail(h, ICWF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); } } while (0)
+  CKI(cudaMemcpyAsync(dpsi, ps.data(), b_psi, cudaMemcpyHostToDevice, h->stream));
+  CKI(cudaMemcpyAsync(dchi, cs.data(), b_chi, cudaMemcpyHostToDevice, h->stream));
+  CKI(cudaMemcpyAsync(dp0, psi0, b_p0, cudaMemcpyHostToDevice, h->stream));
+  CKI(cudaMemcpyAsync(h->x, xs.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
+  CKI(cudaMemcpyAsync(h->R, Rs.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
+  CKI(cudaMemcpyAsync(h->xo, xs.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
+  CKI(cudaMemcpyAsync(h->Ro, Rs.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
+  CKI(cudaMemsetAsync(h->status, 0, 64 * 4, h->stream));
+  launch_init_projection(N, nx, nR, h->dx, h->dR, dpsi, dchi, dp0, h->y, h->stream);
+  if (h->mixed) {
+    launch_to_c64((size_t)N * nx, dpsi, (float2*)h->psi, h->stream);
+    launch_to_c64((size_t)N * nR, dchi, (float2*)h->chi, h->stream);
+  } else {
+    CKI(cudaMemcpyAsync(h->psi, dpsi, b_psi, cudaMemcpyDeviceToDevice, h->stream));
+    CKI(cudaMemcpyAsync(h->chi, dchi, b_chi, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  JobView j = view(h);
+  launch_velocity<double>(j, nullptr, h->stream);   // pinned factor values at x_0, R_0
+  h->cur = 0;
+  assemble(h, h->S[0], h->H[0]);
+  factor(h, h->S[0], h->S[0], 1.0, h->L[0]);
+  solve(h, h->L[0], h->y, h->C, false);
+  st = sync_status(h, "init");
+  cleanup();
+#undef CKI
+  if (st != ICWF_OK) return st;
+  h->initialised = true;
+  h->steps = 0;
+  h->t = 0.0;
+  return ICWF_OK;
+}
+
+icwf_status icwf_init_from_positions(icwf_handle h, const double* psi0, const double* x,
+                                     const double* R) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_init_from_positions: NULL handle");
+  if (!psi0 || !x || !R) return fail(h, ICWF_ERR_ARG, "icwf_init_from_positions: NULL array");
+  std::vector<double> xs(x, x + h->N), Rs(R, R + h->N);
+  return init_common(h, psi0, xs, Rs);
+}
+
+icwf_status icwf_init_from_density(icwf_handle h, const double* psi0, uint64_t seed) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_init_from_density: NULL handle");
+  if (!psi0) return fail(h, ICWF_ERR_ARG, "icwf_init_from_density: psi0 is NULL");
+  const int nx = h->nx, nR = h->nR, N = h->N;
+  const size_t n = (size_t)nx * nR;
+  std::vector<double> cum(n);
+  double c = 0.0;
+  for (size_t e = 0; e < n; ++e) {
+    const double re = psi0[2 * e], im = psi0[2 * e + 1];
+    if (!std::isfinite(re) || !std::isfinite(im))
+      return fail(h, ICWF_ERR_ARG, "icwf_init_from_density: psi0 has a non-finite entry");
+    const double pr = re * re;
+    const double pi = im * im;
+    c = c + (pr + pi);
+    cum[e] = c;
+  }
+  const double total = cum[n - 1];
+  if (!(total > 0)) return fail(h, ICWF_ERR_ARG, "icwf_init_from_density: |psi0|^2 sums to zero");
+  SplitMix64 rng(seed);
+  std::vector<double> xs(N), Rs(N);
+  for (int a = 0; a < N; ++a) {
+    const double target = rng.uniform() * total;
+    size_t idx = (size_t)(std::upper_bound(cum.begin(), cum.end(), target) - cum.begin());
+    if (idx > n - 1) idx = n - 1;
+    const int i = (int)(idx / nR), jj = (int)(idx % nR);
+    const double xi = h->p.x_min + ((double)i + 0.5) * h->dx;
+    const double Rj = h->p.R_min + ((double)jj + 0.5) * h->dR;
+    xs[a] = xi + (rng.uniform() - 0.5) * h->dx;
+    Rs[a] = Rj + (rng.uniform() - 0.5) * h->dR;
+  }
+  return init_common(h, psi0, xs, Rs);
+}
+
+icwf_status icwf_step(icwf_handle h, int32_t n_steps) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_step: NULL handle");
+  if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_step: handle not initialised");
+  if (n_steps < 0) return fail(h, ICWF_ERR_ARG, "icwf_step: n_steps < 0");
+  for (int s = 0; s < n_steps; ++s) step_once(h);
+  CK(cudaGetLastError());
+  return sync_status(h, "icwf_step");
+}
+
+icwf_status icwf_observables(icwf_handle h, icwf_obs* out) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_observables: NULL handle");
+  if (!out) return fail(h, ICWF_ERR_ARG, "icwf_observables: out is NULL");
+  if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_observables: handle not initialised");
+  icwf_status st = alloc_obs(h);
+  if (st) return st;
+  JobView j = view(h);
+  {
+    ProfScope ps(h, F_OBS);
+    if (h->mixed) launch_reconstruct<float>(j, h->C, h->Psi, h->stream);
+    else launch_reconstruct<double>(j, h->C, h->Psi, h->stream);
+    launch_obs_lines(j, h->Psi, h->phi, h->n_states, h->rho_x, h->rho_R, h->proj, h->part,
+                     h->obs_out, h->pop, h->decoh, h->twx_d, h->twR_d, h->stream);
+  }
+  double o4[4];
+  int cl[2];
+  CK(cudaMemcpyAsync(o4, h->obs_out, sizeof(o4), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(cl, h->status, sizeof(cl), cudaMemcpyDeviceToHost, h->stream));
+  if (out->rho_x) CK(cudaMemcpyAsync(out->rho_x, h->rho_x, h->nx * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (out->rho_R) CK(cudaMemcpyAsync(out->rho_R, h->rho_R, h->nR * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (out->pop && h->n_states)
+    CK(cudaMemcpyAsync(out->pop, h->pop, h->n_states * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (out->decoh && h->n_states)
+    CK(cudaMemcpyAsync(out->decoh, h->decoh, h->n_states * h->n_states * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->prof_on) prof_collect(h);
+  out->t = h->t;
+  out->norm = o4[0];
+  out->energy = (o4[1] + o4[2] + o4[3]) / o4[0];
+  out->n_states = h->n_states;
+  out->n_clamped = cl[1];
+  return ICWF_OK;
+}
+
+icwf_status icwf_get_state(icwf_handle h, double* C, double* x, double* R, double* psi,
+                           double* chi) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_get_state: NULL handle");
+  if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_get_state: handle not initialised");
+  CK(cudaStreamSynchronize(h->stream));
+  const int N = h->N;
+  if (C) CK(cudaMemcpy(C, h->C, (size_t)N * 16, cudaMemcpyDeviceToHost));
+  if (x) CK(cudaMemcpy(x, h->x, (size_t)N * 8, cudaMemcpyDeviceToHost));
+  if (R) CK(cudaMemcpy(R, h->R, (size_t)N * 8, cudaMemcpyDeviceToHost));
+  auto grab = [&](const void* src, size_t count, double* dst) -> icwf_status {
+    if (!h->mixed) {
+      CK(cudaMemcpy(dst, src, count * 16, cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<float> f(2 * count);
+      CK(cudaMemcpy(f.data(), src, count * 8, cudaMemcpyDeviceToHost));
+      for (size_t e = 0; e < 2 * count; ++e) dst[e] = f[e];
+    }
+    return ICWF_OK;
+  };
+  if (psi) { icwf_status st = grab(h->psi, (size_t)N * h->nx, psi); if (st) return st; }
+  if (chi) { icwf_status st = grab(h->chi, (size_t)N * h->nR, chi); if (st) return st; }
+  return ICWF_OK;
+}
+
+icwf_status icwf_get_matrices(icwf_handle h, double* S, double* Hout, double* Heff) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_get_matrices: NULL handle");
+  if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_get_matrices: handle not initialised");
+  CK(cudaStreamSynchronize(h->stream));
+  const int N = h->N, nx = h->nx, nR = h->nR;
+  const size_t NN = (size_t)N * N;
+  if (S) CK(cudaMemcpy(S, h->S[h->cur], NN * 16, cudaMemcpyDeviceToHost));
+  if (Heff) CK(cudaMemcpy(Heff, h->H[h->cur], NN * 16, cudaMemcpyDeviceToHost));
+  if (!Hout) return ICWF_OK;
+  // H = T1 o S2 + S1 o T2 + W, W = sum_k s_k A_k o B_k + V1 o S2 + S1 o V2 (diagnostic path)
+  void* tmp = nullptr;
+  const size_t cw = h->cwf_elem;
+  const size_t bytes = align256((size_t)N * nx * cw) + align256((size_t)N * nR * cw) + 9 * align256(NN * 16) + 256;
+  CK(cudaMalloc(&tmp, bytes));
+  Arena a{(char*)tmp, bytes, 0};
+  void* tpsi = a.take((size_t)N * nx * cw);
+  void* tchi = a.take((size_t)N * nR * cw);
+  double2* G[9];
+  for (int q = 0; q < 9; ++q) G[q] = (double2*)a.take(NN * 16);
+  double2 *T1 = G[0], *T2 = G[1], *S1 = G[2], *S2 = G[3], *V1 = G[4], *V2 = G[5], *Wm = G[6],
+          *Ak = G[7], *Bk = G[8];
+  JobView j = view(h);
+  cudaStream_t s = h->stream;
+  if (h->mixed) {
+    launch_kinetic<float>(j, tpsi, tchi, s);
+    launch_gram<float>(h->psi, tpsi, nullptr, nx, N, h->dx, T1, s);
+    launch_gram<float>(h->chi, tchi, nullptr, nR, N, h->dR, T2, s);
+    launch_gram<float>(h->psi, h->psi, nullptr, nx, N, h->dx, S1, s);
+    launch_gram<float>(h->chi, h->chi, nullptr, nR, N, h->dR, S2, s);
+    launch_gram<float>(h->psi, h->psi, h->v1, nx, N, h->dx, V1, s);
+    launch_gram<float>(h->chi, h->chi, h->v2, nR, N, h->dR, V2, s);
+  } else {
+    launch_kinetic<double>(j, tpsi, tchi, s);
+    launch_gram<double>(h->psi, tpsi, nullptr, nx, N, h->dx, T1, s);
+    launch_gram<double>(h->chi, tchi, nullptr, nR, N, h->dR, T2, s);
+    launch_gram<double>(h->psi, h->psi, nullptr, nx, N, h->dx, S1, s);
+    launch_gram<double>(h->chi, h->chi, nullptr, nR, N, h->dR, S2, s);
+    launch_gram<double>(h->psi, h->psi, h->v1, nx, N, h->dx, V1, s);
+    launch_gram<double>(h->chi, h->chi, h->v2, nR, N, h->dR, V2, s);
+  }
+  cudaMemsetAsync(Wm, 0, NN * 16, s);
+  std::vector<double> sk(h->K);
+  cudaMemcpy(sk.data(), h->sig, h->K * 8, cudaMemcpyDeviceToHost);
+  for (int k = 0; k < h->K; ++k) {
+    if (h->mixed) {
+      launch_gram<float>(h->psi, h->psi, h->U + (size_t)k * nx, nx, N, h->dx, Ak, s);
+      launch_gram<float>(h->chi, h->chi, h->W + (size_t)k * nR, nR, N, h->dR, Bk, s);
+    } else {
+      launch_gram<double>(h->psi, h->psi, h->U + (size_t)k * nx, nx, N, h->dx, Ak, s);
+      launch_gram<double>(h->chi, h->chi, h->W + (size_t)k * nR, nR, N, h->dR, Bk, s);
+    }
+    launch_hadamard_acc(N, sk[k], Ak, Bk, Wm, s);
+  }
+  launch_combine_h(N, T1, T2, S1, S2, V1, V2, Wm, Ak, s);
+  cudaError_t e = cudaMemcpyAsync(Hout, Ak, NN * 16, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(h, ICWF_ERR_CUDA, "icwf_get_matrices: copy failed");
+  return ICWF_OK;
+}
+
+icwf_status icwf_get_info(icwf_handle h, icwf_info* out) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_get_info: NULL handle");
+  if (!out) return fail(h, ICWF_ERR_ARG, "icwf_get_info: out is NULL");
+  out->rank = h->K;
+  out->tail_rel = h->tail_rel;
+  out->next_rel = h->next_rel;
+  out->sigma_max = h->sigma_max;
+  out->device_bytes = h->arena.size;
+  out->steps_done = h->steps;
+  out->t = h->t;
+  out->kernel_launches = h->launches;
+  return ICWF_OK;
+}
+
+icwf_status icwf_get_stream(icwf_handle h, void** stream) {
+  if (!h || !stream) return fail(h, ICWF_ERR_ARG, "icwf_get_stream: NULL argument");
+  *stream = (void*)h->stream;
+  return ICWF_OK;
+}
+
+icwf_status icwf_profile_enable(icwf_handle h, int32_t on) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_profile_enable: NULL handle");
+  h->prof_on = on != 0;
+  return ICWF_OK;
+}
+
+icwf_status icwf_profile_reset(icwf_handle h) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_profile_reset: NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  prof_collect(h);
+  for (int f = 0; f < F_COUNT; ++f) { h->prof_ms[f] = 0; h->prof_n[f] = 0; }
+  return ICWF_OK;
+}
+
+icwf_status icwf_profile_read(icwf_handle h, int32_t n, const char** names, double* ms,
+                              int64_t* launches, int32_t* n_out) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_profile_read: NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  prof_collect(h);
+  for (int f = 0; f < F_COUNT && f < n; ++f) {
+    if (names) names[f] = kFamNames[f];
+    if (ms) ms[f] = h->prof_ms[f];
+    if (launches) launches[f] = h->prof_n[f];
+  }
+  if (n_out) *n_out = F_COUNT;
+  return ICWF_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Serving pool
+// ============================================================================================
+
+struct PoolJob {
+  icwf_handle h = nullptr;
+  int64_t target = 0;
+  int state = 0;   // 0 pending, 1 live, 2 finished, 3 failed
+  double norm = 0, energy = 0, t = 0;
+  std::vector<double> rho_x, rho_R, pop, decoh;
+  int n_clamped = 0, n_states = 0;
+};
+
+struct icwf_pool_ctx {
+  size_t budget = 0;
+  int max_jobs = 0;
+  size_t live_bytes = 0;
+  std::vector<PoolJob> jobs;
+  std::deque<int> pending;
+  std::vector<int> live;
+};
+
+extern "C" {
+
+icwf_status icwf_pool_create(size_t hbm_budget_bytes, int32_t max_jobs, icwf_pool* out) {
+  if (!out || max_jobs < 1 || hbm_budget_bytes == 0)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_create: invalid argument");
+  icwf_pool p = new icwf_pool_ctx;
+  p->budget = hbm_budget_bytes;
+  p->max_jobs = max_jobs;
+  *out = p;
+  return ICWF_OK;
+}
+
+icwf_status icwf_pool_submit(icwf_pool pool, icwf_handle job, int64_t n_steps, int32_t* job_id) {
+  if (!pool || !job || n_steps < 0) return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_submit: invalid argument");
+  if (!job->initialised) return fail(nullptr, ICWF_ERR_STATE, "icwf_pool_submit: job not initialised");
+  if (job->arena.size > pool->budget)
+    return fail(nullptr, ICWF_ERR_OOM, "icwf_pool_submit: job footprint exceeds the pool budget");
+  PoolJob pj;
+  pj.h = job;
+  pj.target = job->steps + n_steps;
+  pool->jobs.push_back(std::move(pj));
+  const int id = (int)pool->jobs.size() - 1;
+  pool->pending.push_back(id);
+  if (job_id) *job_id = id;
+  return ICWF_OK;
+}
+
+static void finish_job(icwf_pool pool, int id, bool ok) {
+  PoolJob& j = pool->jobs[id];
+  icwf_handle h = j.h;
+  if (ok) {
+    j.rho_x.assign(h->nx, 0.0);
+    j.rho_R.assign(h->nR, 0.0);
+    j.pop.assign(8, 0.0);
+    j.decoh.assign(64, 0.0);
+    icwf_obs o{};
+    o.rho_x = j.rho_x.data(); o.rho_R = j.rho_R.data(); o.pop = j.pop.data(); o.decoh = j.decoh.data();
+    if (icwf_observables(h, &o) == ICWF_OK) {
+      j.norm = o.norm; j.energy = o.energy; j.t = o.t; j.n_clamped = o.n_clamped;
+      j.n_states = o.n_states;
+      j.state = 2;
+    } else {
+      j.state = 3;
+    }
+  } else {
+    j.state = 3;
+  }
+  pool->live_bytes -= h->arena.size;
+  icwf_destroy(h);
+  j.h = nullptr;
+}
+
+icwf_status icwf_pool_tick(icwf_pool pool, int32_t* n_live, int32_t* n_finished) {
+  if (!pool) return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_tick: NULL pool");
+  // admission in arrival order while slots and memory allow
+  while (!pool->pending.empty() && (int)pool->live.size() < pool->max_jobs) {
+    const int id = pool->pending.front();
+    const size_t b = pool->jobs[id].h->arena.size;
+    if (pool->live_bytes + b > pool->budget) break;
+    pool->pending.pop_front();
+    pool->live.push_back(id);
+    pool->live_bytes += b;
+    pool->jobs[id].state = 1;
+  }
+  // one step of every live job: enqueue all, then wait for all (the jobs' streams overlap)
+  for (int id : pool->live) {
+    PoolJob& j = pool->jobs[id];
+    if (j.h->steps < j.target) step_once(j.h);
+  }
+  int fin = 0;
+  std::vector<int> still;
+  for (int id : pool->live) {
+    PoolJob& j = pool->jobs[id];
+    const icwf_status st = sync_status(j.h, "icwf_pool_tick");
+    if (st != ICWF_OK) { finish_job(pool, id, false); ++fin; continue; }
+    if (j.h->steps >= j.target) { finish_job(pool, id, true); ++fin; continue; }
+    still.push_back(id);
+  }
+  pool->live.swap(still);
+  if (n_live) *n_live = (int)pool->live.size();
+  if (n_finished) *n_finished = fin;
+  return ICWF_OK;
+}
+
+icwf_status icwf_pool_poll(icwf_pool pool, int32_t job_id, icwf_obs* out, int32_t* state) {
+  if (!pool || job_id < 0 || job_id >= (int)pool->jobs.size())
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_poll: invalid job id");
+  PoolJob& j = pool->jobs[job_id];
+  if (state) *state = j.state;
+  if (j.state == 2 && out) {
+    out->t = j.t; out->norm = j.norm; out->energy = j.energy; out->n_clamped = j.n_clamped;
+    out->n_states = j.n_states;
+    if (out->rho_x) std::copy(j.rho_x.begin(), j.rho_x.end(), out->rho_x);
+    if (out->rho_R) std::copy(j.rho_R.begin(), j.rho_R.end(), out->rho_R);
+    if (out->pop) std::copy(j.pop.begin(), j.pop.begin() + j.n_states, out->pop);
+    if (out->decoh) std::copy(j.decoh.begin(), j.decoh.begin() + j.n_states * j.n_states, out->decoh);
+  }
+  return ICWF_OK;
+}
+
+icwf_status icwf_pool_destroy(icwf_pool pool) {
+  if (!pool) return ICWF_OK;
+  for (auto& j : pool->jobs)
+    if (j.h) icwf_destroy(j.h);
+  delete pool;
+  return ICWF_OK;
+}
+
+}  // extern "C"

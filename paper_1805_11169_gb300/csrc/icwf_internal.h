@@ -1,0 +1,129 @@
+// Internal declarations shared by the host orchestration (api.cpp) and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/icwf.h"
+
+namespace icwf {
+
+// Status word bits (device int32 at status[0]); counters follow.
+enum : int {
+  ST_NONFINITE = 1,     // NaN/Inf seen in a velocity, coefficient or matrix
+  ST_CHOL = 2,          // Cholesky pivot <= 0
+  ST_TIMEOUT = 4,       // bounded wait gave up
+  ST_ARG = 8            // kernel saw an out-of-range size
+};
+enum : int { STATUS_FLAGS = 0, STATUS_CLAMPED = 1, STATUS_TICKET = 2, STATUS_WORDS = 8 };
+
+// ---------------------------------------------------------------- launch descriptors
+
+// Device view of one ICWF job's state, passed by value to kernels.  Matrices are row-major
+// N x N complex128 ([a*N + b], a = bra row, b = ket column).  CWFs are column-major:
+// psi[a*nx + i] = psi_a(x_i), chi[a*nR + j] = chi_a(R_j); complex128 (FP64 mode) or complex64.
+struct JobView {
+  int N, nx, nR, K, logx, logR;
+  double x_min, dx, R_min, dR, inv_mx, inv_mR, dt, eps;
+  const double* V;        // nx*nR row-major
+  const void* Vt;         // the same table in the CWF storage precision (float or double)
+  const double* U;        // K*nx  (u_k contiguous)
+  const double* W;        // K*nR
+  const double* sig;      // K
+  const double* v1;       // nx
+  const double* v2;       // nR
+  void* psi;              // N*nx complex
+  void* chi;              // N*nR complex
+  double* x;              // N (positions at the current time)
+  double* R;
+  double* xo;             // N (positions at the previous time; midpoints use both)
+  double* Ro;
+  double* px;             // K*N: u_k(x_b)
+  double* pR;             // K*N: w_k(R_b)
+  double* d;              // N: V(x_b, R_b) from the factors
+  const void* kinx;       // nx bit-reversed kinetic phases / nx
+  const void* kinR;
+  const void* twx;        // nx/2 twiddles exp(-2 pi i k / nx)
+  const void* twR;
+  int* status;
+};
+
+// Per-kernel-family timing hook (api.cpp implements it).
+struct Prof;
+
+// ---------------------------------------------------------------- kernels (launchers)
+
+// a4: velocities (Eq. v1/v2), Euler positions (clamped), pinned factor values at the new
+// positions.  T = CWF storage type.
+template <typename T> void launch_velocity(const JobView& j, const double2* C, cudaStream_t s);
+
+// a1-a3: Strang split-operator step of every psi_a (pinned at the R midpoint) and chi_a (pinned
+// at the x midpoint).  mode 0 = propagate; mode 1 = apply the kinetic operator only (writes to
+// out, diagnostic).
+template <typename T> void launch_propagate(const JobView& j, cudaStream_t s);
+template <typename T> void launch_kinetic(const JobView& j, void* out_psi, void* out_chi,
+                                          cudaStream_t s);
+
+// a5 (FP64): S = S1 o S2 and Heff from the rank-K factors at the current positions.
+void launch_assemble_fp64(const JobView& j, double2* S, double2* H, cudaStream_t s);
+
+// Generic Gram G = scale * A^H diag(dg) B (A, B column-major n x N complex of type T, dg may be
+// NULL for identity); output N x N complex128 row-major.
+template <typename T> void launch_gram(const void* A, const void* B, const double* dg, int n,
+                                       int N, double scale, double2* G, cudaStream_t s);
+
+// Elementwise H = T1 o S2 + S1 o T2 + sum_k sig_k A_k o B_k + V1 o S2 + S1 o V2 (diagnostic).
+void launch_combine_h(int N, const double2* T1, const double2* T2, const double2* S1,
+                      const double2* S2, const double2* V1, const double2* V2, const double2* W,
+                      double2* H, cudaStream_t s);
+void launch_hadamard_acc(int N, double sig, const double2* A, const double2* B, double2* W,
+                         cudaStream_t s);
+
+// a6: regularised Cholesky and RK4.
+// A[m] = (1-theta_m) S0 + theta_m S1 + eps I for the batch of matrices m (full N x N).
+void launch_shift_mix(int N, const double2* S0, const double2* S1, double eps, double theta,
+                      double2* A, cudaStream_t s);
+// Right-looking blocked Cholesky of nbatch matrices in place (lower triangle = L).
+void launch_cholesky(int N, double2* const* A, int nbatch, int* status, cudaStream_t s);
+// y = ((1-theta) H0 + theta H1) (C + c * kp)      (kp may be NULL)
+void launch_matvec(int N, const double2* H0, const double2* H1, double theta, const double2* C,
+                   const double2* kp, double c, double2* y, cudaStream_t s);
+// L z = y (forward) then L^H w = z (backward); out = scale_i * w with scale_i = -i when
+// minus_i, else 1.  work needs 2N complex, flags 2*ceil(N/32) unsigned (zeroed at allocation),
+// tickets 2 unsigned; epoch must differ from every earlier call on the same flags.
+void launch_chol_solve(int N, const double2* L, const double2* y, double2* work, double2* out,
+                       bool minus_i, unsigned* flags, unsigned* tickets, unsigned epoch,
+                       int* status, cudaStream_t s);
+// C += dt/6 (k1 + 2 k2 + 2 k3 + k4); flags non-finite values.
+void launch_rk4_final(int N, double2* C, const double2* k1, const double2* k2,
+                      const double2* k3, const double2* k4, double dt, int* status,
+                      cudaStream_t s);
+void launch_check_finite(int n, const double2* a, int* status, cudaStream_t s);
+
+// a7: observables.
+// Psi[i*nR + j] = sum_a C_a psi_a(x_i) chi_a(R_j)  (complex128 output).
+template <typename T> void launch_reconstruct(const JobView& j, const double2* C, double2* Psi,
+                                              cudaStream_t s);
+// Column / row reductions of Psi: rho_R, rho_x, potential energy, BO projections, FFT kinetic
+// energies (partials), then the final deterministic sums into out[0..3] = norm, ekx, ekR, epot.
+// part needs 2 nR + nx doubles, proj n_states * nR complex; twx/twR are FP64 twiddles.
+void launch_obs_lines(const JobView& j, const double2* Psi, const double* phi, int n_states,
+                      double* rho_x, double* rho_R, double2* proj, double* part, double* out,
+                      double* pop, double* decoh, const double2* twx, const double2* twR,
+                      cudaStream_t s);
+
+// Initial projection b_a = dx dR sum_ij conj(psi_a(x_i) chi_a(R_j)) Psi0[i, j] (FP64 CWFs).
+void launch_init_projection(int N, int nx, int nR, double dx, double dR, const double2* psi,
+                            const double2* chi, const double2* Psi0, double2* b, cudaStream_t s);
+// Convert complex128 -> complex64.
+void launch_to_c64(size_t n, const double2* in, float2* out, cudaStream_t s);
+
+// Mixed-precision assembly on the tensor cores (tcgen05); returns false if unsupported sizes.
+bool launch_assemble_tc(const JobView& j, int kind, double2* S, double2* H, void* scratch,
+                        size_t scratch_bytes, cudaStream_t s);
+size_t assemble_tc_scratch_bytes(int N, int nx, int nR, int K);
+
+}  // namespace icwf

@@ -114,7 +114,7 @@ class Workload:
     n_traj: int
     n_steps: int
     svd_rel_cutoff: float = 0.0
-    s_reg_eps: float = 1e-10
+    s_reg_eps: float = 1e-6
     seed: int = 0
     model: dict = field(default_factory=dict)
     V: np.ndarray | None = None
@@ -148,7 +148,7 @@ def _normalise(psi0, dx, dR):
 
 def shin_metiu(nx=128, x_range=(-50.0, 50.0), nR=64, R_range=(-9.0, 9.0), n_traj=16, dt=0.1,
                n_steps=100, R0=-4.0, width=1.0 / math.sqrt(2.85), Rf=5.0, Rl=3.1, Rr=4.0, L=19.0,
-               mass_R=1836.0, n_states=3, svd_rel_cutoff=0.0, s_reg_eps=1e-10, seed=0,
+               mass_R=1836.0, n_states=3, svd_rel_cutoff=0.0, s_reg_eps=1e-6, seed=0,
                name="shin_metiu") -> Workload:
     """Shin-Metiu PCET: Psi0(x, R) = exp(-(R - R0)^2 / (2 width^2)) phi_1(x; R), normalised."""
     x, dx = cell_grid(nx, *x_range)
@@ -174,7 +174,7 @@ def atom_levels(nx, x_range, n=3):
 
 def cavity(nx=2048, x_range=(-80.0, 80.0), nq=256, q_range=(-30.0, 30.0), lam=0.5,
            n_traj=1024, dt=0.05, n_steps=100, n_states=3, svd_rel_cutoff=1e-12,
-           s_reg_eps=1e-10, seed=0, name="cavity") -> Workload:
+           s_reg_eps=1e-6, seed=0, name="cavity") -> Workload:
     """Electron in a resonant single-mode cavity; Psi0 = phi_1^atom(x) (w/pi)^(1/4) e^{-w q^2/2}."""
     x, dx = cell_grid(nx, *x_range)
     q, dq = cell_grid(nq, *q_range)
