@@ -26,8 +26,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 OBS_EVERY = 100
-MODES = {"fp64": (0, "f64", 1e-12), "bf16x3": (1, "mixed-bf16x3", 1e-8),
-         "tf32x3": (2, "mixed-tf32x3", 1e-8)}
+# mode -> (precision enum, dtype label, SVD cutoff, regulariser eps)
+MODES = {"fp64": (0, "f64", 1e-12, 1e-6), "bf16x3": (1, "mixed-bf16x3", 1e-8, 1e-4),
+         "tf32x3": (2, "mixed-tf32x3", 1e-8, 1e-4)}
 NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 (vector and DMMA alike), nominal
 
 
@@ -37,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fp64", choices=list(MODES))
+    ap.add_argument("--mode", default="tf32x3", choices=list(MODES))
     ap.add_argument("--n-traj", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -45,9 +46,9 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(n_traj, cutoff):
+def make_workload(n_traj, cutoff, eps):
     from workloads import WORKLOADS
-    return WORKLOADS["sm_paper"](n_traj=n_traj, svd_rel_cutoff=cutoff)
+    return WORKLOADS["sm_paper"](n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps)
 
 
 def workload_name(w):
@@ -195,8 +196,8 @@ def run_ours(args, rank, ws, local):
     import paper_1805_11169_gb300 as g
 
     torch.cuda.set_device(local)
-    prec, dtype_name, cutoff = MODES[args.mode]
-    w = make_workload(args.n_traj, cutoff)
+    prec, dtype_name, cutoff, eps = MODES[args.mode]
+    w = make_workload(args.n_traj, cutoff, eps)
     params = g.params_from(w, precision=prec)
 
     sim = g.Icwf(params, w.V)
@@ -259,7 +260,7 @@ def run_ours(args, rank, ws, local):
         "dtype": dtype_name,
         "data": "synthetic (Shin-Metiu potential, BO states and |Psi0|^2 sampling computed here)",
         "config": {"workload": workload_name(w), "nx": w.nx, "nR": w.nR, "n_traj": w.n_traj,
-                   "dt": w.dt, "rank_k": info["rank"], "svd_rel_cutoff": cutoff,
+                   "dt": w.dt, "rank_k": info["rank"], "svd_rel_cutoff": cutoff, "s_reg_eps": eps,
                    "svd_tail_rel": info["tail_rel"], "coeff_scheme": "rk4-interpolated",
                    "obs_every": OBS_EVERY, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
@@ -332,8 +333,8 @@ def run_cpu_baseline(w, budget_s):
 def run_reference(args, rank, ws):
     if rank != 0:
         return None
-    prec, dtype_name, cutoff = MODES[args.mode]
-    w = make_workload(args.n_traj, cutoff)
+    prec, dtype_name, cutoff, eps = MODES[args.mode]
+    w = make_workload(args.n_traj, cutoff, eps)
     from oracle.icwf import Icwf as Oracle, Params
     p = Params(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, w.dt,
                w.n_traj, w.svd_rel_cutoff, w.s_reg_eps)

@@ -1,15 +1,604 @@
-// Mixed-precision matrix-element assembly on the tcgen05 tensor cores (split BF16 / TF32
-// operands, FP32 accumulation in tensor memory).
+// Mixed-precision matrix-element assembly (Eq. M, W, W1, W2) on the sm_103a tensor cores.
+//
+// Each CWF is split into real and imaginary planes, and every plane value v into two pieces of
+// the operand type (v ~ hi + lo; BF16 or TF32).  The Grams G_g = Psi^H diag(u_g) Psi (g = 0 is the
+// overlap, g >= 1 the rank-k interaction terms) become real products of planar operands:
+//   Re G = P^T D P + Q^T D Q,   Im G = P^T D Q - Q^T D P,
+// each evaluated as hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (TMEM).
+//
+// Kernel layout (one CTA per 128 x 32 block of (bra a, ket b) pairs, 192 threads):
+//   warp 4       TMA producer: 128-byte-swizzled tiles of the bra planes (128 rows) and the
+//                ket planes scaled by u_g (32 rows), two pipeline stages;
+//   warp 5       MMA issuer: tcgen05.mma kind::f16 (BF16) or kind::tf32, M = 128, N = 32, into
+//                four accumulators (PP, PQ, QP, QQ) per grid side;
+//   warps 0..3   epilogue: lane = bra a.  g = 0 gives S1, S2 (kept in TMEM); every g >= 1 adds
+//                s_g (A_g - u_g(x_b) S1)(B_g - w_g(R_b) S2) to Heff (and to the mirrored entry
+//                (b, a) for off-diagonal blocks, using u_g(x_a), w_g(R_a)).
+// CTAs are launched only for the upper triangle of 128 x 128 trajectory blocks (Hermitian
+// symmetry of the Grams), four CTAs per block.
+//
+// Every wait on an mbarrier is bounded (globaltimer, 2 s); a timeout sets the status flag, stops
+// issuing work, drains what is in flight (bounded again), frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "icwf_internal.h"
+#include "k_common.cuh"
 
 namespace icwf {
 
-size_t assemble_tc_scratch_bytes(int, int, int, int) { return 0; }
+namespace tc {
 
-bool launch_assemble_tc(const JobView&, int, double2*, double2*, void*, size_t, cudaStream_t) {
-  return false;
+constexpr int BM = 128;        // bra trajectories per CTA (TMEM lanes)
+constexpr int BNT = 32;        // ket trajectories per CTA
+constexpr int ROWB = 128;      // bytes of one operand row per stage (one swizzle atom row)
+constexpr int STAGES = 2;
+constexpr int A_TILE = BM * ROWB;     // 16 KB
+constexpr int B_TILE = BNT * ROWB;    // 4 KB
+// stage layout: A_P_hi, A_P_lo, A_Q_hi, A_Q_lo, B_P_hi, B_P_lo, B_Q_hi, B_Q_lo
+constexpr int STAGE_BYTES = 4 * A_TILE + 4 * B_TILE;   // 80 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 512;
+// TMEM column map: per side s (0 = x, 1 = R) accumulators PP, PQ, QP, QQ at 32 columns each
+constexpr int COL_ACC = 0;       // [0, 256): g accumulators, side-major
+constexpr int COL_S = 256;       // [256, 384): S1 (re, im) for 32 kets, then S2 (re, im)
+constexpr int COL_H = 384;       // [384, 512): Heff (re, im) and the mirrored entries (re, im)
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+struct Args {
+  int N, nx, nR, K;
+  float dx, dR;
+  const double* sig;
+  const double* px;   // K*N
+  const double* pR;
+  const double* d;    // N
+  double2* S;
+  double2* H;
+  int* status;
+  int kind;           // 0 bf16, 1 tf32
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; returns false (and raises the abort flag) on timeout or if another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag,
+                                         int* status) {
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_test(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtime() - t0 > WAIT_NS) {
+      *abort_flag = 1;
+      set_flag(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading-dimension offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride between 8-row groups
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = BF16 (kind 0) or TF32 (kind 1), both K-major,
+// M = 128, N = 32.
+__host__ __device__ constexpr uint32_t idesc(int kind) {
+  return (1u << 4) | ((kind ? 2u : 1u) << 7) | ((kind ? 2u : 1u) << 10) | ((uint32_t)(BNT >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc(0)), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 8 consecutive 32-bit TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+struct Maps {
+  CUtensorMap xhi_a, xlo_a, Rhi_a, Rlo_a;   // 128-row boxes (bra planes)
+  CUtensorMap xhi_b, xlo_b, Rhi_b, Rlo_b;   // 32-row boxes (ket planes)
+};
+
+// Block (I <= J) of 128 x 128 trajectories and ket quarter q from the linear CTA index.
+__device__ __forceinline__ void block_index(int t, int& I, int& J, int& q) {
+  q = t & 3;
+  t >>= 2;
+  int Jc = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (Jc * (Jc + 1) / 2 > t) --Jc;
+  while ((Jc + 1) * (Jc + 2) / 2 <= t) ++Jc;
+  J = Jc;
+  I = t - Jc * (Jc + 1) / 2;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_constant__ Maps maps) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int I, J, q;
+  block_index(blockIdx.x, I, J, q);
+  const int N = args.N;
+  const int a0 = I * BM;               // bra trajectories a0 .. a0+127
+  const int b0 = J * BM + q * BNT;     // ket trajectories b0 .. b0+31
+  const int G = args.K + 1;
+  const int stx = (args.nx * (KIND ? 4 : 2) + ROWB - 1) / ROWB;   // pipeline stages per Gram
+  const int stR = (args.nR * (KIND ? 4 : 2) + ROWB - 1) / ROWB;
+  const int kel = ROWB / (KIND ? 4 : 2);                           // K elements per stage
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 128);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int last_it[STAGES];
+#pragma unroll
+  for (int t = 0; t < STAGES; ++t) last_it[t] = -1;
+  if (warp == 4) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int it = 0;
+      for (int g = 0; g < G && !*abort_flag; ++g) {
+        for (int side = 0; side < 2 && !*abort_flag; ++side) {
+          const CUtensorMap* mha = side ? &maps.Rhi_a : &maps.xhi_a;
+          const CUtensorMap* mla = side ? &maps.Rlo_a : &maps.xlo_a;
+          const CUtensorMap* mhb = side ? &maps.Rhi_b : &maps.xhi_b;
+          const CUtensorMap* mlb = side ? &maps.Rlo_b : &maps.xlo_b;
+          const int nst = side ? stR : stx;
+          for (int s = 0; s < nst; ++s, ++it) {
+            const int slot = it % STAGES;
+            const unsigned ph = (unsigned)(it / STAGES) & 1u;
+            if (!mbar_wait(empty + slot, ph ^ 1u, abort_flag, args.status)) break;
+            unsigned char* st = smem + slot * STAGE_BYTES;
+            mbar_expect_tx(full + slot, STAGE_BYTES);
+            last_it[slot] = it;
+            const int kc = s * kel;
+            // bra planes (g = 0 rows): P rows [0, N), Q rows [N, 2N)
+            tma_load_2d(st + 0 * A_TILE, mha, kc, a0, full + slot);
+            tma_load_2d(st + 1 * A_TILE, mla, kc, a0, full + slot);
+            tma_load_2d(st + 2 * A_TILE, mha, kc, N + a0, full + slot);
+            tma_load_2d(st + 3 * A_TILE, mla, kc, N + a0, full + slot);
+            // ket planes scaled by u_g: rows (2g) N + b and (2g+1) N + b
+            unsigned char* sb = st + 4 * A_TILE;
+            tma_load_2d(sb + 0 * B_TILE, mhb, kc, 2 * g * N + b0, full + slot);
+            tma_load_2d(sb + 1 * B_TILE, mlb, kc, 2 * g * N + b0, full + slot);
+            tma_load_2d(sb + 2 * B_TILE, mhb, kc, (2 * g + 1) * N + b0, full + slot);
+            tma_load_2d(sb + 3 * B_TILE, mlb, kc, (2 * g + 1) * N + b0, full + slot);
+          }
+        }
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int it = 0;
+      for (int g = 0; g < G && !*abort_flag; ++g) {
+        if (g >= 1) {
+          // the epilogue must have consumed the previous Gram's accumulators
+          if (!mbar_wait(acc_empty, (unsigned)(g - 1) & 1u, abort_flag, args.status)) break;
+          fence_after();
+        }
+        for (int side = 0; side < 2 && !*abort_flag; ++side) {
+          const uint32_t acc = tmem + COL_ACC + side * 128;
+          const int nst = side ? stR : stx;
+          for (int s = 0; s < nst; ++s, ++it) {
+            const int slot = it % STAGES;
+            const unsigned ph = (unsigned)(it / STAGES) & 1u;
+            if (!mbar_wait(full + slot, ph, abort_flag, args.status)) break;
+            fence_after();
+            const uint32_t st = smem_u32(smem + slot * STAGE_BYTES);
+            const uint32_t aph = st, apl = st + A_TILE, aqh = st + 2 * A_TILE, aql = st + 3 * A_TILE;
+            const uint32_t sb = st + 4 * A_TILE;
+            const uint32_t bph = sb, bpl = sb + B_TILE, bqh = sb + 2 * B_TILE, bql = sb + 3 * B_TILE;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = kk * 32;   // 32 bytes of K per instruction
+              const uint32_t first = (s == 0 && kk == 0) ? 0u : 1u;
+              // PP, PQ, QP, QQ, each hi*hi + hi*lo + lo*hi
+              mma<KIND>(acc + 0, sdesc(aph + o), sdesc(bph + o), first);
+              mma<KIND>(acc + 0, sdesc(aph + o), sdesc(bpl + o), 1u);
+              mma<KIND>(acc + 0, sdesc(apl + o), sdesc(bph + o), 1u);
+              mma<KIND>(acc + 32, sdesc(aph + o), sdesc(bqh + o), first);
+              mma<KIND>(acc + 32, sdesc(aph + o), sdesc(bql + o), 1u);
+              mma<KIND>(acc + 32, sdesc(apl + o), sdesc(bqh + o), 1u);
+              mma<KIND>(acc + 64, sdesc(aqh + o), sdesc(bph + o), first);
+              mma<KIND>(acc + 64, sdesc(aqh + o), sdesc(bpl + o), 1u);
+              mma<KIND>(acc + 64, sdesc(aql + o), sdesc(bph + o), 1u);
+              mma<KIND>(acc + 96, sdesc(aqh + o), sdesc(bqh + o), first);
+              mma<KIND>(acc + 96, sdesc(aqh + o), sdesc(bql + o), 1u);
+              mma<KIND>(acc + 96, sdesc(aql + o), sdesc(bqh + o), 1u);
+            }
+            mma_commit(empty + slot);   // frees the stage when these MMAs complete
+          }
+        }
+        mma_commit(acc_full);           // Gram g complete (both sides)
+      }
+      mma_commit(drain);                // every MMA issued by this CTA
+    }
+  } else {
+    // ---------------- epilogue: warps 0..3, lane = bra row ----------------
+    const int row = warp * 32 + lane;
+    const int a = a0 + row;
+    const bool a_ok = a < N;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const bool mirror = I != J;
+    const float dx = args.dx, dR = args.dR;
+    for (int g = 0; g < G; ++g) {
+      const bool ok = mbar_wait(acc_full, (unsigned)g & 1u, abort_flag, args.status);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      fence_after();
+      const float sg = g ? (float)args.sig[g - 1] : 0.f;
+      const float uxa = (g && a_ok) ? (float)args.px[(size_t)(g - 1) * N + a] : 0.f;
+      const float wRa = (g && a_ok) ? (float)args.pR[(size_t)(g - 1) * N + a] : 0.f;
+#pragma unroll 1
+      for (int c8 = 0; c8 < BNT; c8 += 8) {
+        float xpp[8], xpq[8], xqp[8], xqq[8], rpp[8], rpq[8], rqp[8], rqq[8];
+        tmem_ld8(lane_base + COL_ACC + 0 + c8, xpp);
+        tmem_ld8(lane_base + COL_ACC + 32 + c8, xpq);
+        tmem_ld8(lane_base + COL_ACC + 64 + c8, xqp);
+        tmem_ld8(lane_base + COL_ACC + 96 + c8, xqq);
+        tmem_ld8(lane_base + COL_ACC + 128 + c8, rpp);
+        tmem_ld8(lane_base + COL_ACC + 160 + c8, rpq);
+        tmem_ld8(lane_base + COL_ACC + 192 + c8, rqp);
+        tmem_ld8(lane_base + COL_ACC + 224 + c8, rqq);
+        tmem_wait_ld();
+        float Ar[8], Ai[8], Br[8], Bi[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          Ar[e] = dx * (xpp[e] + xqq[e]);
+          Ai[e] = dx * (xpq[e] - xqp[e]);
+          Br[e] = dR * (rpp[e] + rqq[e]);
+          Bi[e] = dR * (rpq[e] - rqp[e]);
+        }
+        if (g == 0) {
+          // S1 = <psi_a|psi_b>, S2 = <chi_a|chi_b>, kept in TMEM for every later Gram;
+          // the Heff accumulators start at zero
+          float zero[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) zero[e] = 0.f;
+          tmem_st8(lane_base + COL_S + c8, Ar);
+          tmem_st8(lane_base + COL_S + 32 + c8, Ai);
+          tmem_st8(lane_base + COL_S + 64 + c8, Br);
+          tmem_st8(lane_base + COL_S + 96 + c8, Bi);
+          tmem_st8(lane_base + COL_H + c8, zero);
+          tmem_st8(lane_base + COL_H + 32 + c8, zero);
+          tmem_st8(lane_base + COL_H + 64 + c8, zero);
+          tmem_st8(lane_base + COL_H + 96 + c8, zero);
+          tmem_wait_st();
+        } else {
+          float s1r[8], s1i[8], s2r[8], s2i[8], hr[8], hi[8], tr[8], ti[8];
+          tmem_ld8(lane_base + COL_S + c8, s1r);
+          tmem_ld8(lane_base + COL_S + 32 + c8, s1i);
+          tmem_ld8(lane_base + COL_S + 64 + c8, s2r);
+          tmem_ld8(lane_base + COL_S + 96 + c8, s2i);
+          tmem_ld8(lane_base + COL_H + c8, hr);
+          tmem_ld8(lane_base + COL_H + 32 + c8, hi);
+          tmem_ld8(lane_base + COL_H + 64 + c8, tr);
+          tmem_ld8(lane_base + COL_H + 96 + c8, ti);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int b = b0 + c8 + e;
+            const bool b_ok = b < N;
+            const float uxb = b_ok ? (float)args.px[(size_t)(g - 1) * N + b] : 0.f;
+            const float wRb = b_ok ? (float)args.pR[(size_t)(g - 1) * N + b] : 0.f;
+            // (A - u(x_b) S1) (B - w(R_b) S2)
+            const float atr = Ar[e] - uxb * s1r[e], ati = Ai[e] - uxb * s1i[e];
+            const float btr = Br[e] - wRb * s2r[e], bti = Bi[e] - wRb * s2i[e];
+            hr[e] = fmaf(sg, atr * btr - ati * bti, hr[e]);
+            hi[e] = fmaf(sg, atr * bti + ati * btr, hi[e]);
+            if (mirror) {
+              // entry (b, a): conj(A) - u(x_a) conj(S1), conj(B) - w(R_a) conj(S2)
+              const float mtr = Ar[e] - uxa * s1r[e], mti = -(Ai[e] - uxa * s1i[e]);
+              const float ntr = Br[e] - wRa * s2r[e], nti = -(Bi[e] - wRa * s2i[e]);
+              tr[e] = fmaf(sg, mtr * ntr - mti * nti, tr[e]);
+              ti[e] = fmaf(sg, mtr * nti + mti * ntr, ti[e]);
+            }
+          }
+          tmem_st8(lane_base + COL_H + c8, hr);
+          tmem_st8(lane_base + COL_H + 32 + c8, hi);
+          tmem_st8(lane_base + COL_H + 64 + c8, tr);
+          tmem_st8(lane_base + COL_H + 96 + c8, ti);
+          tmem_wait_st();
+        }
+      }
+      fence_before();
+      mbar_arrive(acc_empty);
+    }
+    // final: S = S1 o S2; Heff(a, b) = H - d_b S; Heff(b, a) = HT - d_a conj(S)
+    const int aborted = __shfl_sync(0xffffffffu, *abort_flag, 0);
+    if (!aborted) {
+      const double da = a_ok ? args.d[a] : 0.0;
+#pragma unroll 1
+      for (int c8 = 0; c8 < BNT; c8 += 8) {
+        float s1r[8], s1i[8], s2r[8], s2i[8], hr[8], hi[8], tr[8], ti[8];
+        tmem_ld8(lane_base + COL_S + c8, s1r);
+        tmem_ld8(lane_base + COL_S + 32 + c8, s1i);
+        tmem_ld8(lane_base + COL_S + 64 + c8, s2r);
+        tmem_ld8(lane_base + COL_S + 96 + c8, s2i);
+        tmem_ld8(lane_base + COL_H + c8, hr);
+        tmem_ld8(lane_base + COL_H + 32 + c8, hi);
+        tmem_ld8(lane_base + COL_H + 64 + c8, tr);
+        tmem_ld8(lane_base + COL_H + 96 + c8, ti);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int b = b0 + c8 + e;
+          if (b >= N || !a_ok) continue;
+          const double sr = (double)s1r[e] * s2r[e] - (double)s1i[e] * s2i[e];
+          const double si = (double)s1r[e] * s2i[e] + (double)s1i[e] * s2r[e];
+          const double db = args.d[b];
+          args.S[(size_t)a * N + b] = make_double2(sr, si);
+          args.H[(size_t)a * N + b] = make_double2(hr[e] - db * sr, hi[e] - db * si);
+          if (mirror) {
+            args.S[(size_t)b * N + a] = make_double2(sr, -si);
+            args.H[(size_t)b * N + a] = make_double2(tr[e] - da * sr, ti[e] + da * si);
+          }
+        }
+      }
+    }
+  }
+
+  // ---------------- teardown ----------------
+  __syncthreads();
+  if (warp == 5 && lane == 0) {
+    // wait (bounded) until every issued MMA has retired before TMEM is released
+    const unsigned long long t0 = gtime();
+    while (!mbar_test(drain, 0u) && gtime() - t0 < WAIT_NS) {
+    }
+  }
+  if (warp == 4 && lane == 0 && *abort_flag) {
+    // bounded drain of TMA copies that may still be landing in shared memory: wait for the
+    // phase of the last copy issued into each stage
+    for (int t = 0; t < STAGES; ++t) {
+      if (last_it[t] < 0) continue;
+      const unsigned ph = (unsigned)(last_it[t] / STAGES) & 1u;
+      const unsigned long long t0 = gtime();
+      while (!mbar_test(full + t, ph) && gtime() - t0 < WAIT_NS) {
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------- operand prep
+
+// Planar split operands for one grid side: rows r = (2g + comp) N + b, K index i contiguous:
+// value = comp(psi_b(x_i)) * (g ? u_{g-1}(x_i) : 1), split into hi + lo of the operand type.
+template <int KIND>
+__global__ void k_prep(const float2* __restrict__ cwf, const double* __restrict__ U, int n, int N,
+                       int G, void* __restrict__ hi_out, void* __restrict__ lo_out) {
+  const size_t total = (size_t)G * N * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n);
+    const size_t gb = e / n;
+    const int b = (int)(gb % N);
+    const int g = (int)(gb / N);
+    const float2 z = cwf[(size_t)b * n + i];
+    const float u = g ? (float)U[(size_t)(g - 1) * n + i] : 1.0f;
+    const float vr = z.x * u, vi = z.y * u;
+    const size_t rp = ((size_t)(2 * g) * N + b) * n + i;
+    const size_t rq = ((size_t)(2 * g + 1) * N + b) * n + i;
+    if (KIND == 0) {
+      __nv_bfloat16* H = (__nv_bfloat16*)hi_out;
+      __nv_bfloat16* L = (__nv_bfloat16*)lo_out;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hq = __float2bfloat16_rn(vi);
+      H[rp] = hr;
+      L[rp] = __float2bfloat16_rn(vr - __bfloat162float(hr));
+      H[rq] = hq;
+      L[rq] = __float2bfloat16_rn(vi - __bfloat162float(hq));
+    } else {
+      // TF32: keep the top 10 mantissa bits (round to nearest), the remainder as the low piece
+      float* H = (float*)hi_out;
+      float* L = (float*)lo_out;
+      auto r19 = [](float v) {
+        uint32_t u32 = __float_as_uint(v);
+        u32 = (u32 + 0x1000u) & 0xFFFFE000u;
+        return __uint_as_float(u32);
+      };
+      const float hr = r19(vr), hq = r19(vi);
+      H[rp] = hr;
+      L[rp] = r19(vr - hr);
+      H[rq] = hq;
+      L[rq] = r19(vi - hq);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* base, int kind, int n, size_t rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const size_t esz = kind ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(n * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, kind ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+bool launch_assemble_tc(const JobView& j, int precision, double2* S, double2* H, void* scratch,
+                        size_t scratch_bytes, cudaStream_t s) {
+  using namespace tc;
+  const int kind = precision == ICWF_MIXED_TF32X3 ? 1 : 0;
+  const size_t esz = kind ? 4 : 2;
+  const int G = j.K + 1;
+  const size_t rx = (size_t)2 * G * j.N, nxe = rx * j.nx * esz, nRe = rx * j.nR * esz;
+  auto al = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
+  if (2 * al(nxe) + 2 * al(nRe) > scratch_bytes) return false;
+  char* p = (char*)scratch;
+  void* xhi = p; p += al(nxe);
+  void* xlo = p; p += al(nxe);
+  void* Rhi = p; p += al(nRe);
+  void* Rlo = p; p += al(nRe);
+  const int threads = 256;
+  auto grid_for = [&](size_t n) { size_t g = (n + threads - 1) / threads; return (unsigned)(g > 8192 ? 8192 : g); };
+  const size_t totx = (size_t)G * j.N * j.nx, totR = (size_t)G * j.N * j.nR;
+  if (kind) {
+    k_prep<1><<<grid_for(totx), threads, 0, s>>>((const float2*)j.psi, j.U, j.nx, j.N, G, xhi, xlo);
+    k_prep<1><<<grid_for(totR), threads, 0, s>>>((const float2*)j.chi, j.W, j.nR, j.N, G, Rhi, Rlo);
+  } else {
+    k_prep<0><<<grid_for(totx), threads, 0, s>>>((const float2*)j.psi, j.U, j.nx, j.N, G, xhi, xlo);
+    k_prep<0><<<grid_for(totR), threads, 0, s>>>((const float2*)j.chi, j.W, j.nR, j.N, G, Rhi, Rlo);
+  }
+  Maps m;
+  bool ok = make_map(&m.xhi_a, xhi, kind, j.nx, rx, BM) && make_map(&m.xlo_a, xlo, kind, j.nx, rx, BM) &&
+            make_map(&m.Rhi_a, Rhi, kind, j.nR, rx, BM) && make_map(&m.Rlo_a, Rlo, kind, j.nR, rx, BM) &&
+            make_map(&m.xhi_b, xhi, kind, j.nx, rx, BNT) && make_map(&m.xlo_b, xlo, kind, j.nx, rx, BNT) &&
+            make_map(&m.Rhi_b, Rhi, kind, j.nR, rx, BNT) && make_map(&m.Rlo_b, Rlo, kind, j.nR, rx, BNT);
+  if (!ok) return false;
+  Args a;
+  a.N = j.N; a.nx = j.nx; a.nR = j.nR; a.K = j.K;
+  a.dx = (float)j.dx; a.dR = (float)j.dR;
+  a.sig = j.sig; a.px = j.px; a.pR = j.pR; a.d = j.d;
+  a.S = S; a.H = H; a.status = j.status; a.kind = kind;
+  const int T = (j.N + BM - 1) / BM;
+  const unsigned grid = (unsigned)(4 * T * (T + 1) / 2);
+  if (kind) {
+    cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    k_gram_tc<1><<<grid, 192, SMEM_BYTES, s>>>(a, m);
+  } else {
+    cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    k_gram_tc<0><<<grid, 192, SMEM_BYTES, s>>>(a, m);
+  }
+  return true;
+}
+
+size_t assemble_tc_scratch_bytes(int N, int nx, int nR, int K) {
+  // hi + lo planes (P and Q rows for every Gram) for both sides, TF32 (4 bytes) as the larger
+  const size_t G = (size_t)K + 1;
+  return 2 * 4 * G * 2 * (size_t)N * ((size_t)nx + nR) + 4 * 1024;
 }
 
 }  // namespace icwf

@@ -1,0 +1,96 @@
+"""Mixed-precision path (complex64 CWFs, FP32 propagation, tensor-core Grams as split BF16 or TF32
+products with FP32 accumulation; FP64 solve) against the FP64 oracle.
+
+The tensor cores accumulate in FP32, which leaves rounding noise of about 1e-6 relative in S;
+its spectral norm exceeds the FP64 default regulariser (1e-6), so the mixed modes run with
+eps = 1e-4 (above that noise floor), and the FP64 oracle they are compared with uses the same eps.
+
+Bars:
+* per step, S and Heff within 1e-5 relative Frobenius of the FP64 formulas evaluated on the
+  same (complex64) CWFs and positions: this isolates the tensor-core assembly;
+* after a run, the electronic and nuclear densities and the BO populations within 1e-3 L1 of
+  the FP64 oracle run from the same initial state.
+"""
+import numpy as np
+import pytest
+
+from oracle.icwf import Icwf as Oracle, Params
+from workloads import cavity, shin_metiu
+
+pytestmark = pytest.mark.gpu
+
+g = pytest.importorskip("paper_1805_11169_gb300")
+
+MODES = {"bf16x3": 1, "tf32x3": 2}
+EPS_MIXED = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_for(w):
+    return Oracle(Params(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, w.dt,
+                         w.n_traj, w.svd_rel_cutoff, w.s_reg_eps), w.V)
+
+
+def assembly_error(sim, w):
+    st = sim.state()
+    m = sim.matrices()
+    o = oracle_for(w)
+    S = o.overlaps(st["psi"], st["chi"])[2]
+    H = o.heff_factorised(st["psi"], st["chi"], st["x"], st["R"])
+    return rel(m["S"], S), rel(m["Heff"], H)
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("N", [16, 37, 130])
+def test_tensor_core_assembly_per_step(mode, N):
+    """Ragged N (partial 32-wide ket blocks, two 128-wide bra blocks at N = 130)."""
+    w = shin_metiu(nx=128, x_range=(-50.0, 50.0), nR=64, R_range=(-9.0, 9.0), n_traj=N, dt=0.1,
+                   svd_rel_cutoff=1e-8, s_reg_eps=EPS_MIXED)
+    sim = g.Icwf(g.params_from(w, precision=MODES[mode]), w.V)
+    sim.init_from_density(w.psi0, 0)
+    eS, eH = assembly_error(sim, w)
+    assert eS < 1e-5 and eH < 1e-5, (eS, eH)
+    sim.step(3)
+    eS, eH = assembly_error(sim, w)
+    assert eS < 1e-5 and eH < 1e-5, (eS, eH)
+    S = sim.matrices()["S"]
+    assert np.max(np.abs(S - S.conj().T)) < 1e-6
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_cavity_rank_one_assembly(mode):
+    w = cavity(nx=256, x_range=(-40.0, 40.0), nq=64, q_range=(-15.0, 15.0), n_traj=64, dt=0.05,
+               svd_rel_cutoff=1e-8, s_reg_eps=EPS_MIXED)
+    sim = g.Icwf(g.params_from(w, precision=MODES[mode]), w.V)
+    sim.init_from_density(w.psi0, 0)
+    sim.step(2)
+    eS, eH = assembly_error(sim, w)
+    assert eS < 1e-5 and eH < 1e-5, (eS, eH)
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_mixed_observables_vs_fp64_oracle(mode):
+    """Shin-Metiu 128 x 64, N = 32, 100 steps of dt = 0.1, rank cutoff 1e-8: densities and
+    populations within 1e-3 L1 of the FP64 oracle."""
+    w = shin_metiu(n_traj=32, svd_rel_cutoff=1e-8, s_reg_eps=EPS_MIXED)
+    o = oracle_for(w)
+    ost = o.init_from_density(w.psi0, 0)
+    for _ in range(100):
+        o.step(ost)
+    oo = o.observables(ost, w.phi)
+    sim = g.Icwf(g.params_from(w, precision=MODES[mode]), w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, 0)
+    sim.step(100)
+    ob = sim.observables()
+    l1x = w.dx * np.sum(np.abs(ob["rho_x"] - oo["rho_x"]))
+    l1R = w.dR * np.sum(np.abs(ob["rho_R"] - oo["rho_R"]))
+    l1p = np.sum(np.abs(ob["pop"] - oo["pop"]))
+    assert l1x < 1e-3 and l1R < 1e-3 and l1p < 1e-3, (l1x, l1R, l1p)
+    assert abs(ob["norm"] - oo["norm"]) < 1e-3
+    sim.close()
