@@ -78,6 +78,8 @@ struct icwf_ctx {
   double2 *y = nullptr, *work = nullptr;
   double2 *S[2] = {nullptr, nullptr}, *H[2] = {nullptr, nullptr};
   double2 *L[2] = {nullptr, nullptr}, *Lh = nullptr;
+  double *invL[2] = {nullptr, nullptr}, *invLh = nullptr;   // reciprocal Cholesky pivots
+  double2 *DL[2] = {nullptr, nullptr}, *DLh = nullptr;       // inverted 32 x 32 diagonal blocks
   unsigned *flags = nullptr, *tickets = nullptr;
   int* status = nullptr;
   int cur = 0;
@@ -264,23 +266,25 @@ icwf_status sync_status(icwf_ctx* h, const char* where) {
   return ICWF_OK;
 }
 
-// Factor L[dst] = chol(S_src + eps I) (theta selects the mix of S[cur] and S[nxt]).
-void factor(icwf_ctx* h, const double2* S0, const double2* S1, double theta, double2* dst) {
+// Factor the batch dst[m] = chol((1 - theta_m) S0_m + theta_m S1_m + eps I), m < n <= 2: both
+// matrices go through the same launches, so their factorisations overlap on the device.
+void factor(icwf_ctx* h, int n, const double2* const* S0, const double2* const* S1,
+            const double* theta, double2* const* dst, double* const* inv, double2* const* D) {
   {
     ProfScope ps(h, F_SHIFT);
-    launch_shift_mix(h->N, S0, S1, h->p.s_reg_eps, theta, dst, h->stream);
+    for (int m = 0; m < n; ++m)
+      launch_shift_mix(h->N, S0[m], S1[m], h->p.s_reg_eps, theta[m], dst[m], h->stream);
+    h->launches += n;
   }
   ProfScope ps(h, F_POTRF);
-  double2* arr[2] = {dst, dst};
-  launch_cholesky(h->N, arr, 1, h->status, h->stream);
-  const int T = (h->N + 31) / 32;
-  h->launches += 1 + (3 * T - 2);   // shift + potrf/trsm/herk per panel
+  h->launches += launch_cholesky(h->N, dst, inv, D, n, h->status, h->stream);
 }
 
-void solve(icwf_ctx* h, const double2* Lf, const double2* y, double2* out, bool minus_i) {
+void solve(icwf_ctx* h, const double2* Lf, const double2* D, const double2* y, double2* out,
+           bool minus_i) {
   ProfScope ps(h, F_SOLVE);
   ++h->epoch;
-  launch_chol_solve(h->N, Lf, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
+  launch_chol_solve(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
                     h->status, h->stream);
   h->launches += 2;
 }
@@ -315,6 +319,8 @@ void step_once(icwf_ctx* h) {
   }
   assemble(h, h->S[nxt], h->H[nxt]);
   double2 *Lc = h->L[cur], *Ln = h->L[nxt];
+  double *ic = h->invL[cur], *in = h->invL[nxt];
+  double2 *Dc = h->DL[cur], *Dn = h->DL[nxt];
   if (h->p.coeff_scheme == 1) {
     // S, Heff frozen at t_n over the step: every stage uses L[cur], H[cur]
     for (int st = 0; st < 4; ++st) {
@@ -325,14 +331,25 @@ void step_once(icwf_ctx* h) {
                       h->stream);
         h->launches += 1;
       }
-      solve(h, Lc, h->y, h->kk[st], true);
+      solve(h, Lc, Dc, h->y, h->kk[st], true);
     }
-    factor(h, h->S[nxt], h->S[nxt], 1.0, Ln);
+    const double2* s0[1] = {h->S[nxt]};
+    const double th[1] = {1.0};
+    double2* d[1] = {Ln};
+    double* iv[1] = {in};
+    double2* dd[1] = {Dn};
+    factor(h, 1, s0, s0, th, d, iv, dd);
   } else {
-    factor(h, h->S[cur], h->S[nxt], 0.5, h->Lh);
-    factor(h, h->S[nxt], h->S[nxt], 1.0, Ln);
+    const double2* s0[2] = {h->S[cur], h->S[nxt]};
+    const double2* s1[2] = {h->S[nxt], h->S[nxt]};
+    const double th[2] = {0.5, 1.0};
+    double2* d[2] = {h->Lh, Ln};
+    double* iv[2] = {h->invLh, in};
+    double2* dd[2] = {h->DLh, Dn};
+    factor(h, 2, s0, s1, th, d, iv, dd);
     const double thetas[4] = {0.0, 0.5, 0.5, 1.0};
     const double2* Ls[4] = {Lc, h->Lh, h->Lh, Ln};
+    const double2* Is[4] = {Dc, h->DLh, h->DLh, Dn};
     for (int st = 0; st < 4; ++st) {
       const double c = st == 0 ? 0.0 : (st == 3 ? dt : 0.5 * dt);
       {
@@ -341,7 +358,7 @@ void step_once(icwf_ctx* h) {
                       c, h->y, h->stream);
         h->launches += 1;
       }
-      solve(h, Ls[st], h->y, h->kk[st], true);
+      solve(h, Ls[st], Is[st], h->y, h->kk[st], true);
     }
   }
   {
@@ -494,6 +511,8 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
       (size_t)N * 8 * 4, (size_t)K * N * 8 * 2, (size_t)N * 8,
       (size_t)N * 16 * 8,  // C, k1..k4, y, work(2N)
       NN * 16 * 7,         // S[2], H[2], L[2], Lh
+      (size_t)N * 8, (size_t)N * 8, (size_t)N * 8,   // reciprocal pivots of L[2], Lh
+      (size_t)N * 512, (size_t)N * 512, (size_t)N * 512,   // inverted diagonal blocks
       (size_t)2 * nblk * 4 + 64, 64 * 4};
   size_t total = 0;
   for (size_t b : sizes) total += align256(b);
@@ -540,6 +559,12 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
     h->L[q] = (double2*)a.take(NN * 16);
   }
   h->Lh = (double2*)a.take(NN * 16);
+  h->invL[0] = (double*)a.take((size_t)N * 8);
+  h->invL[1] = (double*)a.take((size_t)N * 8);
+  h->invLh = (double*)a.take((size_t)N * 8);
+  h->DL[0] = (double2*)a.take((size_t)N * 512);
+  h->DL[1] = (double2*)a.take((size_t)N * 512);
+  h->DLh = (double2*)a.take((size_t)N * 512);
   h->flags = (unsigned*)a.take((size_t)2 * nblk * 4 + 64);
   h->tickets = h->flags + 2 * nblk;
   h->status = (int*)a.take(64 * 4);
@@ -696,8 +721,15 @@ static icwf_status init_common(icwf_handle h, const double* psi0, const std::vec
   launch_velocity<double>(j, nullptr, h->stream);   // pinned factor values at x_0, R_0
   h->cur = 0;
   assemble(h, h->S[0], h->H[0]);
-  factor(h, h->S[0], h->S[0], 1.0, h->L[0]);
-  solve(h, h->L[0], h->y, h->C, false);
+  {
+    const double2* s0[1] = {h->S[0]};
+    const double th[1] = {1.0};
+    double2* d[1] = {h->L[0]};
+    double* iv[1] = {h->invL[0]};
+    double2* dd[1] = {h->DL[0]};
+    factor(h, 1, s0, s0, th, d, iv, dd);
+  }
+  solve(h, h->L[0], h->DL[0], h->y, h->C, false);
   st = sync_status(h, "init");
   cleanup();
 #undef CKI

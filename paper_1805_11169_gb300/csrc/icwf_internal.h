@@ -86,17 +86,20 @@ void launch_hadamard_acc(int N, double sig, const double2* A, const double2* B, 
 // A[m] = (1-theta_m) S0 + theta_m S1 + eps I for the batch of matrices m (full N x N).
 void launch_shift_mix(int N, const double2* S0, const double2* S1, double eps, double theta,
                       double2* A, cudaStream_t s);
-// Right-looking blocked Cholesky of nbatch matrices in place (lower triangle = L).
-void launch_cholesky(int N, double2* const* A, int nbatch, int* status, cudaStream_t s);
+// Right-looking blocked Cholesky of nbatch <= 2 matrices in place (lower triangle = L); inv[m]
+// receives the N reciprocal pivots 1/L_cc and D[m] (N x 32 complex) the inverses of the 32 x 32
+// diagonal blocks.  Returns the number of kernels launched.
+int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const* D, int nbatch,
+                    int* status, cudaStream_t s);
 // y = ((1-theta) H0 + theta H1) (C + c * kp)      (kp may be NULL)
 void launch_matvec(int N, const double2* H0, const double2* H1, double theta, const double2* C,
                    const double2* kp, double c, double2* y, cudaStream_t s);
 // L z = y (forward) then L^H w = z (backward); out = scale_i * w with scale_i = -i when
 // minus_i, else 1.  work needs 2N complex, flags 2*ceil(N/32) unsigned (zeroed at allocation),
 // tickets 2 unsigned; epoch must differ from every earlier call on the same flags.
-void launch_chol_solve(int N, const double2* L, const double2* y, double2* work, double2* out,
-                       bool minus_i, unsigned* flags, unsigned* tickets, unsigned epoch,
-                       int* status, cudaStream_t s);
+void launch_chol_solve(int N, const double2* L, const double2* D, const double2* y, double2* work,
+                       double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
+                       unsigned epoch, int* status, cudaStream_t s);
 // C += dt/6 (k1 + 2 k2 + 2 k3 + k4); flags non-finite values.
 void launch_rk4_final(int N, double2* C, const double2* k1, const double2* k2,
                       const double2* k3, const double2* k4, double dt, int* status,

@@ -43,85 +43,132 @@ void launch_shift_mix(int N, const double2* S0, const double2* S1, double eps, d
 
 // ------------------------------------------------------------------------------ Cholesky
 
-struct MatBatch { double2* m[2]; };
+struct MatBatch { double2* m[2]; double* inv[2]; double2* D[2]; };
 
-// Factor the diagonal block jb of each matrix (one CTA per matrix).  Rows/columns beyond N are
-// treated as identity so that ragged sizes factor cleanly.
-__global__ void __launch_bounds__(256) k_potrf_diag(int N, MatBatch mb, int jb, int* status) {
-  __shared__ double2 L[NB][NB + 1];
+// Factor the diagonal block jb of each matrix: one warp per matrix, lane r holds row r of the
+// block in registers.  Column c: pivot d = A_cc, 1/sqrt(d) by rsqrt, L_cc = d * rsqrt(d);
+// L_rc *= rsqrt(d) for r > c; rank-1 update of the trailing block with column c broadcast by
+// shuffles.  The reciprocal pivots are stored for the panel and triangular solves.  Rows and
+// columns beyond N are treated as identity so that ragged sizes factor cleanly.
+__global__ void __launch_bounds__(32) k_potrf_diag(int N, MatBatch mb, int jb, int* status) {
   double2* A = mb.m[blockIdx.y];
+  double* inv = mb.inv[blockIdx.y];
+  const int r = threadIdx.x;
   const int r0 = jb * NB;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
-    if (r0 + r < N && r0 + c < N) v = A[(size_t)(r0 + r) * N + r0 + c];
-    L[r][c] = v;
-  }
-  __syncthreads();
+  const bool rok = r0 + r < N;
+  double2 L[NB];
+#pragma unroll
   for (int c = 0; c < NB; ++c) {
-    if (threadIdx.x == 0) {
-      double d = L[c][c].x;
+    double2 v = make_double2(c == r ? 1.0 : 0.0, 0.0);
+    if (rok && r0 + c < N && c <= r) v = A[(size_t)(r0 + r) * N + r0 + c];
+    L[c] = v;
+  }
+  double my_inv = 1.0;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    double dinv = 0.0;
+    if (r == c) {
+      double d = L[c].x;
       if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
-      L[c][c] = make_double2(sqrt(d), 0.0);
+      dinv = rsqrt(d);
+      L[c] = make_double2(d * dinv, 0.0);
+      my_inv = dinv;
     }
-    __syncthreads();
-    const double inv = 1.0 / L[c][c].x;
-    for (int r = c + 1 + threadIdx.x; r < NB; r += blockDim.x) L[r][c] = cscale(L[r][c], inv);
-    __syncthreads();
-    const int m = NB - 1 - c;   // trailing size
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int r = c + 1 + e / m, q = c + 1 + e % m;
-      if (q <= r) {
+    dinv = __shfl_sync(0xffffffffu, dinv, c);
+    if (r > c) L[c] = cscale(L[c], dinv);
+#pragma unroll
+    for (int q = c + 1; q < NB; ++q) {
+      double2 lq;
+      lq.x = __shfl_sync(0xffffffffu, L[c].x, q);
+      lq.y = __shfl_sync(0xffffffffu, L[c].y, q);
+      if (r >= q) {
         // L[r][q] -= L[r][c] * conj(L[q][c])
-        const double2 a = L[r][c], b = L[q][c];
-        L[r][q].x -= a.x * b.x + a.y * b.y;
-        L[r][q].y -= a.y * b.x - a.x * b.y;
+        L[q].x -= L[c].x * lq.x + L[c].y * lq.y;
+        L[q].y -= L[c].y * lq.x - L[c].x * lq.y;
       }
     }
-    __syncthreads();
   }
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    if (c <= r && r0 + r < N && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = L[r][c];
+  if (rok) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c <= r && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = L[c];
+    inv[r0 + r] = my_inv;
   }
 }
 
-// Panel solve A_ib <- A_ib L_bb^-H for every block row i > jb (one CTA per block row).
-__global__ void __launch_bounds__(256) k_trsm_panel(int N, MatBatch mb, int jb) {
-  __shared__ double2 L[NB][NB + 1];
-  __shared__ double2 X[NB][NB + 1];
+constexpr int TR_WARPS = 8;   // rows per panel-solve CTA
+
+// Panel solve A_ib <- A_ib L_bb^-H below the diagonal block jb: one warp per row, lane = column.
+// Column-oriented substitution: x_m = a_m / L_mm, then a_c -= x_m conj(L_cm) for c > m.
+__global__ void __launch_bounds__(TR_WARPS * 32) k_trsm_panel(int N, MatBatch mb, int jb) {
+  __shared__ double2 Ls[NB][NB + 1];
+  __shared__ double invs[NB];
   double2* A = mb.m[blockIdx.y];
-  const int ib = jb + 1 + blockIdx.x;
-  const int r0 = ib * NB, c0 = jb * NB;
+  const double* inv = mb.inv[blockIdx.y];
+  const int c0 = jb * NB;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
-    double2 l = make_double2(r == c ? 1.0 : 0.0, 0.0);
-    if (c0 + r < N && c0 + c < N && c <= r) l = A[(size_t)(c0 + r) * N + c0 + c];
-    if (c > r) l = make_double2(0.0, 0.0);
-    L[r][c] = l;
-    double2 x = make_double2(0.0, 0.0);
-    if (r0 + r < N && c0 + c < N) x = A[(size_t)(r0 + r) * N + c0 + c];
-    X[r][c] = x;
+    double2 l = make_double2(0.0, 0.0);
+    if (c < r && c0 + r < N && c0 + c < N) l = A[(size_t)(c0 + r) * N + c0 + c];
+    Ls[r][c] = l;
   }
+  if (threadIdx.x < NB) invs[threadIdx.x] = (c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : 1.0;
   __syncthreads();
-  for (int c = 0; c < NB; ++c) {
-    const double inv = 1.0 / L[c][c].x;
-    if (threadIdx.x < NB) X[threadIdx.x][c] = cscale(X[threadIdx.x][c], inv);
-    __syncthreads();
-    const int m = NB - 1 - c;
-    for (int e = threadIdx.x; e < NB * m; e += blockDim.x) {
-      const int r = e / m, q = c + 1 + e % m;
-      // X[r][q] -= X[r][c] * conj(L[q][c])
-      const double2 a = X[r][c], b = L[q][c];
-      X[r][q].x -= a.x * b.x + a.y * b.y;
-      X[r][q].y -= a.y * b.x - a.x * b.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = (jb + 1) * NB + blockIdx.x * TR_WARPS + warp;
+  if (row >= N) return;
+  const bool cok = c0 + lane < N;
+  double2 a = cok ? A[(size_t)row * N + c0 + lane] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int m = 0; m < NB; ++m) {
+    double2 x = cscale(a, invs[m]);
+    x.x = __shfl_sync(0xffffffffu, x.x, m);
+    x.y = __shfl_sync(0xffffffffu, x.y, m);
+    if (lane == m) a = x;
+    else if (lane > m) {
+      const double2 l = Ls[lane][m];
+      a.x -= x.x * l.x + x.y * l.y;   // a -= x conj(l)
+      a.y -= x.y * l.x - x.x * l.y;
     }
-    __syncthreads();
   }
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    if (r0 + r < N && c0 + c < N) A[(size_t)(r0 + r) * N + c0 + c] = X[r][c];
+  if (cok) A[(size_t)row * N + c0 + lane] = a;
+}
+
+// Inverse of every diagonal block after the factorisation: D_b = L_bb^-1 (lower triangular,
+// 32 x 32), stored row-major per block in D[(b*32 + r)*32 + c].  One warp per block, lane = column
+// c of D: D_rc = (delta_rc - sum_{c<=m<r} L_rm D_mc) / L_rr for r >= c.  The triangular solves use
+// these blocks as matrix-vector products, which keeps the dependent substitution chain off their
+// critical path.
+__global__ void __launch_bounds__(32) k_trtri_diag(int N, MatBatch mb) {
+  __shared__ double2 Ls[NB][NB + 1];
+  __shared__ double invs[NB];
+  const double2* A = mb.m[blockIdx.y];
+  const double* inv = mb.inv[blockIdx.y];
+  double2* D = mb.D[blockIdx.y];
+  const int jb = blockIdx.x, r0 = jb * NB, c = threadIdx.x;
+  for (int r = 0; r < NB; ++r) {
+    double2 l = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    if (c < r && r0 + r < N && r0 + c < N) l = A[(size_t)(r0 + r) * N + r0 + c];
+    Ls[r][c] = l;
   }
+  invs[c] = (r0 + c < N) ? inv[r0 + c] : 1.0;
+  __syncwarp();
+  double2 d[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    double2 acc = make_double2(r == c ? 1.0 : 0.0, 0.0);
+#pragma unroll
+    for (int m = 0; m < r; ++m) {
+      // only m >= c contributes (D_mc = 0 for m < c); the loop stays uniform across lanes
+      const double2 l = Ls[r][m];
+      acc.x -= l.x * d[m].x - l.y * d[m].y;
+      acc.y -= l.x * d[m].y + l.y * d[m].x;
+    }
+    d[r] = (r >= c) ? cscale(acc, invs[r]) : make_double2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (r0 + r < N) D[((size_t)jb * NB + r) * NB + c] = d[r];
 }
 
 __device__ __forceinline__ void tri_index_l(int t, int& I, int& J) {
@@ -175,19 +222,30 @@ __global__ void __launch_bounds__(256) k_herk_update(int N, MatBatch mb, int jb)
     }
 }
 
-void launch_cholesky(int N, double2* const* A, int nbatch, int* status, cudaStream_t s) {
+int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const* D, int nbatch,
+                    int* status, cudaStream_t s) {
   MatBatch mb;
   mb.m[0] = A[0];
   mb.m[1] = nbatch > 1 ? A[1] : A[0];
+  mb.inv[0] = inv[0];
+  mb.inv[1] = nbatch > 1 ? inv[1] : inv[0];
+  mb.D[0] = D[0];
+  mb.D[1] = nbatch > 1 ? D[1] : D[0];
   const int T = (N + NB - 1) / NB;
+  int launches = 0;
   for (int jb = 0; jb < T; ++jb) {
-    k_potrf_diag<<<dim3(1, nbatch), 256, 0, s>>>(N, mb, jb, status);
+    k_potrf_diag<<<dim3(1, nbatch), 32, 0, s>>>(N, mb, jb, status);
+    ++launches;
     const int rest = T - jb - 1;
     if (rest > 0) {
-      k_trsm_panel<<<dim3(rest, nbatch), 256, 0, s>>>(N, mb, jb);
+      const int rows = N - (jb + 1) * NB;
+      k_trsm_panel<<<dim3((rows + TR_WARPS - 1) / TR_WARPS, nbatch), TR_WARPS * 32, 0, s>>>(N, mb, jb);
       k_herk_update<<<dim3(rest * (rest + 1) / 2, nbatch), 256, 0, s>>>(N, mb, jb);
+      launches += 2;
     }
   }
+  k_trtri_diag<<<dim3(T, nbatch), 32, 0, s>>>(N, mb);
+  return launches + 1;
 }
 
 // ------------------------------------------------------------------------------ matvec
@@ -231,7 +289,7 @@ void launch_matvec(int N, const double2* H0, const double2* H1, double theta, co
 __device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned epoch, int* status) {
   for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
     if (ld_acquire(f) == epoch) return true;
-    __nanosleep(64);
+    if (it > 4096) __nanosleep(64);   // pure spin first: the expected wait is a few microseconds
   }
   set_flag(status, ST_TIMEOUT);
   return false;
@@ -239,34 +297,43 @@ __device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned epoch, int
 
 constexpr int TW = 8;   // warps per triangular-solve CTA
 
-// Forward solve L z = y.  CTAs take block rows in ticket order (a CTA only waits on block rows
-// with smaller tickets, which are already running or done).  Warp w of the CTA accumulates the
-// off-diagonal products of block columns m = w, w + TW, ...; warp 0 then substitutes within the
-// diagonal block and publishes z_jb with a release flag.  Each lane first loads its 32 matrix
-// entries of a block into registers (independent loads in flight together), then combines them
-// with z broadcast by shuffles.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Forward solve L z = y with the inverted diagonal blocks D_b = L_bb^-1:
+//   z_b = D_b (y_b - sum_{m<b} L_bm z_m).
+// CTAs take block rows in ticket order (a CTA only waits on block rows with smaller tickets,
+// which are already running or done).  Warp 0 owns the critical product with block b-1 and the
+// diagonal product; warps 1.. take the older blocks.  Lane r holds row r; matrix entries are
+// loaded into registers before the wait so that only shuffles and FMAs follow the flag.
 __global__ void __launch_bounds__(TW * 32) k_trsv_lower(int N, const double2* __restrict__ L,
+                                                       const double2* __restrict__ D,
                                                        const double2* __restrict__ y,
                                                        double2* __restrict__ z, unsigned* flags,
                                                        unsigned* ticket, unsigned epoch,
                                                        int* status) {
   __shared__ double2 part[TW][NB];
+  __shared__ double2 Ds[NB][NB + 1];
   __shared__ int s_jb;
   if (threadIdx.x == 0) s_jb = (int)atomicAdd(ticket, 1u);
   __syncthreads();
   const int jb = s_jb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = jb * NB;
-  double2 acc = make_double2(0, 0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Ds[r][c] = (r0 + r < N) ? D[((size_t)jb * NB + r) * NB + c] : make_double2(0, 0);
+  }
   const bool row_ok = r0 + lane < N;
   const double2* Lrow = L + (size_t)(row_ok ? r0 + lane : 0) * N;
-  for (int m = warp; m < jb; m += TW) {
+  double2 acc = make_double2(0, 0);
+  // warps 1..TW-1: blocks m = 0 .. jb-2, round robin
+  for (int m = warp - 1; warp > 0 && m < jb - 1; m += TW - 1) {
     double2 lv[NB];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) lv[c] = __ldg(Lrow + m * NB + c);   // columns < jb*NB <= N
+    for (int c = 0; c < NB; ++c) lv[c] = __ldg(Lrow + m * NB + c);
     if (lane == 0) wait_flag(flags + m, epoch, status);
     __syncwarp();
-    const double2 zm = __ldcg(z + m * NB + lane);   // block m < jb is complete: in range
+    const double2 zm = __ldcg(z + m * NB + lane);
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       double2 zc;
@@ -275,46 +342,57 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_lower(int N, const double2* __
       cfma(acc, lv[c], zc);
     }
   }
-  if (!row_ok) acc = make_double2(0, 0);
-  part[warp][lane] = acc;
+  if (warp > 0) part[warp][lane] = row_ok ? acc : make_double2(0, 0);
   __syncthreads();
-  if (warp == 0) {
-    const int r = lane;
-    double2 v = make_double2(0, 0);
-    if (r0 + r < N) v = y[r0 + r];
-    for (int w = 0; w < TW; ++w) v = csub(v, part[w][r]);
-    double2 lrow[NB];
+  if (warp != 0) return;
+  // warp 0: prefetch the critical block (jb-1), then wait for z_{jb-1}
+  double2 lv[NB];
+  const int mc = jb - 1;
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      double2 l = make_double2(c == r ? 1.0 : 0.0, 0.0);
-      if (r0 + r < N && r0 + c < N && c <= r) l = L[(size_t)(r0 + r) * N + r0 + c];
-      lrow[c] = l;
-    }
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      double2 zc = v;
-      if (r == c) zc = cscale(v, 1.0 / lrow[c].x);
-      zc.x = __shfl_sync(0xffffffffu, zc.x, c);
-      zc.y = __shfl_sync(0xffffffffu, zc.y, c);
-      if (r == c) v = zc;
-      else if (r > c) v = csub(v, cmul(lrow[c], zc));
-    }
-    if (r0 + r < N) z[r0 + r] = v;
-    __threadfence();
+  for (int c = 0; c < NB; ++c) lv[c] = (mc >= 0) ? __ldg(Lrow + mc * NB + c) : make_double2(0, 0);
+  double2 v = row_ok ? y[r0 + lane] : make_double2(0, 0);
+  for (int w = 1; w < TW; ++w) v = csub(v, part[w][lane]);
+  if (mc >= 0) {
+    if (lane == 0) wait_flag(flags + mc, epoch, status);
     __syncwarp();
-    if (lane == 0) st_release(flags + jb, epoch);
+    const double2 zm = __ldcg(z + mc * NB + lane);
+    double2 p = make_double2(0, 0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 zc;
+      zc.x = __shfl_sync(0xffffffffu, zm.x, c);
+      zc.y = __shfl_sync(0xffffffffu, zm.y, c);
+      cfma(p, lv[c], zc);
+    }
+    if (row_ok) v = csub(v, p);
   }
+  // z_jb = D_jb v
+  double2 out = make_double2(0, 0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    double2 vc;
+    vc.x = __shfl_sync(0xffffffffu, v.x, c);
+    vc.y = __shfl_sync(0xffffffffu, v.y, c);
+    cfma(out, Ds[lane][c], vc);
+  }
+  if (row_ok) z[r0 + lane] = out;
+  fence_acq_rel_gpu();
+  __syncwarp();
+  if (lane == 0) st_release(flags + jb, epoch);
 }
 
-// Backward solve L^H w = z, block rows in reverse ticket order; out = w or -i w.  Lane r of a
-// warp reads column r0 + r of the block rows below (coalesced across lanes).
+// Backward solve L^H w = z, block rows in reverse ticket order:
+//   w_b = D_b^H (z_b - sum_{m>b} L_mb^H w_m);  out = w or -i w.
+// Lane r of a warp reads column r0 + r of the block rows below (coalesced across lanes).
 __global__ void __launch_bounds__(TW * 32) k_trsv_upper(int N, const double2* __restrict__ L,
+                                                       const double2* __restrict__ D,
                                                        const double2* __restrict__ z,
                                                        double2* __restrict__ w_out, bool minus_i,
                                                        double2* __restrict__ wbuf, unsigned* flags,
                                                        unsigned* ticket, unsigned epoch,
                                                        int* status) {
   __shared__ double2 part[TW][NB];
+  __shared__ double2 Ds[NB][NB + 1];
   __shared__ int s_jb;
   const int nblk = (N + NB - 1) / NB;
   if (threadIdx.x == 0) s_jb = nblk - 1 - (int)atomicAdd(ticket, 1u);
@@ -322,9 +400,14 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_upper(int N, const double2* __
   const int jb = s_jb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = jb * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Ds[r][c] = (r0 + r < N) ? D[((size_t)jb * NB + r) * NB + c] : make_double2(0, 0);
+  }
   const bool col_ok = r0 + lane < N;
   double2 acc = make_double2(0, 0);
-  for (int m = jb + 1 + warp; m < nblk; m += TW) {
+  // warps 1..TW-1: blocks m = jb+2 .. nblk-1
+  for (int m = jb + 2 + (warp - 1); warp > 0 && m < nblk; m += TW - 1) {
     double2 lv[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
@@ -343,49 +426,59 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_upper(int N, const double2* __
       cfmac(acc, lv[c], wc);
     }
   }
-  part[warp][lane] = acc;
+  if (warp > 0) part[warp][lane] = acc;
   __syncthreads();
-  if (warp == 0) {
-    const int r = lane;
-    double2 v = make_double2(0, 0);
-    if (r0 + r < N) v = z[r0 + r];
-    for (int w = 0; w < TW; ++w) v = csub(v, part[w][r]);
-    // column r of the diagonal block: lcol[q] = L[r0 + q][r0 + r] (q >= r)
-    double2 lcol[NB];
+  if (warp != 0) return;
+  const int mc = jb + 1;
+  double2 lv[NB];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      double2 l = make_double2(q == r ? 1.0 : 0.0, 0.0);
-      if (r0 + r < N && r0 + q < N && q >= r) l = L[(size_t)(r0 + q) * N + r0 + r];
-      lcol[q] = l;
-    }
-    // w_q for q from NB-1 down: w_q = v_q / L_qq; v_r -= conj(L[q][r]) w_q for r < q
-#pragma unroll
-    for (int q = NB - 1; q >= 0; --q) {
-      double2 wq = v;
-      if (r == q) wq = cscale(v, 1.0 / lcol[q].x);
-      wq.x = __shfl_sync(0xffffffffu, wq.x, q);
-      wq.y = __shfl_sync(0xffffffffu, wq.y, q);
-      if (r == q) v = wq;
-      else if (r < q) v = csub(v, cmulc(lcol[q], wq));
-    }
-    if (r0 + r < N) {
-      wbuf[r0 + r] = v;
-      w_out[r0 + r] = minus_i ? make_double2(v.y, -v.x) : v;
-    }
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release(flags + jb, epoch);
+  for (int c = 0; c < NB; ++c) {
+    double2 l = make_double2(0, 0);
+    if (mc < nblk && mc * NB + c < N && col_ok) l = __ldg(L + (size_t)(mc * NB + c) * N + r0 + lane);
+    lv[c] = l;
   }
+  double2 v = col_ok ? z[r0 + lane] : make_double2(0, 0);
+  for (int w = 1; w < TW; ++w) v = csub(v, part[w][lane]);
+  if (mc < nblk) {
+    if (lane == 0) wait_flag(flags + mc, epoch, status);
+    __syncwarp();
+    const double2 wm = (mc * NB + lane < N) ? __ldcg(wbuf + mc * NB + lane) : make_double2(0, 0);
+    double2 p = make_double2(0, 0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      double2 wc;
+      wc.x = __shfl_sync(0xffffffffu, wm.x, c);
+      wc.y = __shfl_sync(0xffffffffu, wm.y, c);
+      cfmac(p, lv[c], wc);
+    }
+    v = csub(v, p);
+  }
+  // w_jb = D_jb^H v: w_r = sum_c conj(D_cr) v_c
+  double2 out = make_double2(0, 0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    double2 vc;
+    vc.x = __shfl_sync(0xffffffffu, v.x, c);
+    vc.y = __shfl_sync(0xffffffffu, v.y, c);
+    cfmac(out, Ds[c][lane], vc);
+  }
+  if (col_ok) {
+    wbuf[r0 + lane] = out;
+    w_out[r0 + lane] = minus_i ? make_double2(out.y, -out.x) : out;
+  }
+  fence_acq_rel_gpu();
+  __syncwarp();
+  if (lane == 0) st_release(flags + jb, epoch);
 }
 
-void launch_chol_solve(int N, const double2* L, const double2* y, double2* work, double2* out,
-                       bool minus_i, unsigned* flags, unsigned* tickets, unsigned epoch,
-                       int* status, cudaStream_t s) {
+void launch_chol_solve(int N, const double2* L, const double2* D, const double2* y, double2* work,
+                       double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
+                       unsigned epoch, int* status, cudaStream_t s) {
   const int nblk = (N + NB - 1) / NB;
   cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
-  k_trsv_lower<<<nblk, TW * 32, 0, s>>>(N, L, y, work, flags, tickets, epoch, status);
+  k_trsv_lower<<<nblk, TW * 32, 0, s>>>(N, L, D, y, work, flags, tickets, epoch, status);
   // work[0, N) holds z; work[N, 2N) holds w for the backward pass's consumers
-  k_trsv_upper<<<nblk, TW * 32, 0, s>>>(N, L, work, out, minus_i, work + N, flags + nblk,
+  k_trsv_upper<<<nblk, TW * 32, 0, s>>>(N, L, D, work, out, minus_i, work + N, flags + nblk,
                                         tickets + 1, epoch, status);
 }
 
