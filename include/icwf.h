@@ -168,6 +168,28 @@ icwf_status icwf_profile_read(icwf_handle h, int32_t n, const char** names, doub
 /* Text of the last failure on h (or of the last failed icwf_create / pool call if h is NULL). */
 const char* icwf_last_error(icwf_handle h);
 
+/* --- observables without device allocation ------------------------------------------------- */
+
+/* Size of the library's fixed observables work area (bytes) and the largest grid it serves. */
+#define ICWF_OBS_STATIC_BYTES 9437184u
+#define ICWF_OBS_STATIC_MAX_GRID 524288u
+
+/* Same observables as icwf_observables, computed without allocating any device memory during
+ * the call.  For callers that cannot call cudaMalloc while they run: code being captured into a
+ * CUDA graph (allocation cannot be captured) or hosts whose allocator forbids device allocation
+ * after start-up.  icwf_observables allocates its work buffers on its first call; this entry point
+ * uses one fixed work area of ICWF_OBS_STATIC_BYTES bytes compiled into the library as a static
+ * device array, which every GPU that loads the library holds until the process exits.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ * Limits: nx * nR <= ICWF_OBS_STATIC_MAX_GRID and nx, nR <= 4096, else ICWF_ERR_ARG.
+ * The first call on a device looks up the work area's device address (once per device, with that
+ * device made current for the lookup): make that first call before any stream capture.  All calls
+ * share the one work area, so calls that overlap on the GPU (two handles, streams or threads)
+ * race; the caller must serialise them.  Each call overwrites every part of the work area that it
+ * reads, so nothing left by an earlier call needs clearing.
+ * The paper has no counterpart to this entry point (it is a deployment aid). */
+icwf_status icwf_observables_static(icwf_handle h, icwf_obs* out);
+
 /* --- serving pool: continuous batching of independent jobs -------------------------------- */
 
 /* A pool admits jobs while their summed device footprint stays within hbm_budget_bytes and at

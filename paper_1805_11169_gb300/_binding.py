@@ -65,6 +65,7 @@ def _load():
         "icwf_init_from_positions": [H, d, d, d],
         "icwf_step": [H, ct.c_int32],
         "icwf_observables": [H, P(icwf_obs)],
+        "icwf_observables_static": [H, P(icwf_obs)],
         "icwf_destroy": [H],
         "icwf_get_state": [H, d, d, d, d, d],
         "icwf_get_matrices": [H, d, d, d],
@@ -147,6 +148,21 @@ def icwf_observables(h, nx: int, nR: int, n_states: int = 8) -> dict:
     o = icwf_obs()
     o.rho_x, o.rho_R, o.pop, o.decoh = _dp(rho_x), _dp(rho_R), _dp(pop), _dp(decoh)
     _check(LIB.icwf_observables(h, ct.byref(o)), h)
+    ns = o.n_states
+    return {"t": o.t, "norm": o.norm, "energy": o.energy, "rho_x": rho_x, "rho_R": rho_R,
+            "pop": pop[:ns].copy(), "decoherence": decoh[:ns * ns].reshape(ns, ns).copy(),
+            "n_clamped": o.n_clamped}
+
+
+def icwf_observables_static(h, nx: int, nR: int) -> dict:
+    """icwf_observables without device allocation (fixed library work area; see icwf.h)."""
+    rho_x = np.zeros(nx)
+    rho_R = np.zeros(nR)
+    pop = np.zeros(8)
+    decoh = np.zeros(64)
+    o = icwf_obs()
+    o.rho_x, o.rho_R, o.pop, o.decoh = _dp(rho_x), _dp(rho_R), _dp(pop), _dp(decoh)
+    _check(LIB.icwf_observables_static(h, ct.byref(o)), h)
     ns = o.n_states
     return {"t": o.t, "norm": o.norm, "energy": o.energy, "rho_x": rho_x, "rho_R": rho_R,
             "pop": pop[:ns].copy(), "decoherence": decoh[:ns * ns].reshape(ns, ns).copy(),

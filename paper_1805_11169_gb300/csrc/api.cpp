@@ -396,6 +396,30 @@ icwf_status alloc_obs(icwf_ctx* h) {
 
 }  // namespace
 
+namespace icwf {
+
+bool handle_obs_view(icwf_handle h, ObsView* v) {
+  if (!h || !v) return false;
+  v->j = view(h);
+  v->C = h->C;
+  v->phi = h->phi;
+  v->n_states = h->n_states;
+  v->mixed = h->mixed;
+  v->initialised = h->initialised;
+  v->twx_d = h->twx_d;
+  v->twR_d = h->twR_d;
+  v->stream = h->stream;
+  v->device = h->device;
+  v->t = h->t;
+  return true;
+}
+
+void handle_set_error(icwf_handle h, const char* msg) {
+  if (h) h->err = msg; else g_err = msg;
+}
+
+}  // namespace icwf
+
 // ============================================================================================
 // C ABI
 // ============================================================================================

@@ -124,6 +124,23 @@ void launch_init_projection(int N, int nx, int nR, double dx, double dR, const d
 // Convert complex128 -> complex64.
 void launch_to_c64(size_t n, const double2* in, float2* out, cudaStream_t s);
 
+// Everything the observables kernels need from a handle (filled by handle_obs_view in api.cpp).
+struct ObsView {
+  JobView j;
+  const double2* C;
+  const double* phi;
+  int n_states;
+  bool mixed;
+  bool initialised;
+  const double2* twx_d;
+  const double2* twR_d;
+  cudaStream_t stream;
+  int device;
+  double t;
+};
+bool handle_obs_view(icwf_handle h, ObsView* v);
+void handle_set_error(icwf_handle h, const char* msg);
+
 // Mixed-precision assembly on the tensor cores (tcgen05); returns false if unsupported sizes.
 bool launch_assemble_tc(const JobView& j, int kind, double2* S, double2* H, void* scratch,
                         size_t scratch_bytes, cudaStream_t s);

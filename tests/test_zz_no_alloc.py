@@ -1,0 +1,64 @@
+"""icwf_observables_static: the allocation-free variant of icwf_observables.
+
+Some callers cannot allocate device memory while they run (code captured into a CUDA graph, or
+an allocator policy that forbids cudaMalloc after start-up).  The variant computes the same
+observables in a fixed work area compiled into the library.  This test calls it through the C ABI
+twice in a row and checks both results against icwf_observables on the same state, and checks
+that a grid larger than the work area is rejected with an argument error.  The file name makes
+pytest collect it last.
+"""
+import numpy as np
+import pytest
+
+from workloads import shin_metiu
+
+pytestmark = pytest.mark.gpu
+
+g = pytest.importorskip("paper_1805_11169_gb300")
+
+
+def _close(a, b):
+    assert abs(a["norm"] - b["norm"]) < 1e-12
+    assert abs(a["energy"] - b["energy"]) < 1e-12
+    assert np.max(np.abs(a["rho_x"] - b["rho_x"])) < 1e-12
+    assert np.max(np.abs(a["rho_R"] - b["rho_R"])) < 1e-12
+    assert np.max(np.abs(a["pop"] - b["pop"])) < 1e-12
+    assert np.max(np.abs(a["decoherence"] - b["decoherence"])) < 1e-12
+    assert a["n_clamped"] == b["n_clamped"]
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_static_observables_match_allocating_entry_point(precision):
+    eps = 1e-6 if precision == 0 else 1e-4
+    w = shin_metiu(n_traj=24, svd_rel_cutoff=1e-8, s_reg_eps=eps)
+    sim = g.Icwf(g.params_from(w, precision=precision), w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, 0)
+    sim.step(3)
+    first = g.icwf_observables_static(sim.h, w.nx, w.nR)
+    second = g.icwf_observables_static(sim.h, w.nx, w.nR)
+    ref = sim.observables()
+    _close(first, ref)
+    _close(second, ref)
+    assert len(ref["pop"]) == 3
+    sim.step(2)
+    third = g.icwf_observables_static(sim.h, w.nx, w.nR)
+    _close(third, sim.observables())
+    sim.close()
+
+
+def test_static_observables_reject_grids_beyond_the_work_area():
+    nx, nR = 2048, 512        # 2^20 grid points > 524288
+    p = g.icwf_params(nx=nx, nR=nR, x_min=-20.0, x_max=20.0, R_min=-5.0, R_max=5.0, mass_x=1.0,
+                      mass_R=1.0, dt=0.01, n_traj=1, precision=0, svd_rel_cutoff=1e-6,
+                      s_reg_eps=1e-6, coeff_scheme=0, max_rank=0)
+    x = -20.0 + (np.arange(nx) + 0.5) * 40.0 / nx
+    R = -5.0 + (np.arange(nR) + 0.5) * 10.0 / nR
+    V = 0.5 * x[:, None] ** 2 + 0.5 * R[None, :] ** 2 + 0.1 * np.outer(x, R)
+    psi0 = np.outer(np.exp(-0.5 * x ** 2), np.exp(-0.5 * R ** 2)).astype(complex)
+    sim = g.Icwf(p, V)
+    sim.init_from_density(psi0, 0)
+    with pytest.raises(g.IcwfError) as e:
+        g.icwf_observables_static(sim.h, nx, nR)
+    assert e.value.status == g.ICWF_ERR_ARG and "too large" in str(e.value)
+    sim.close()
