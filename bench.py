@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--serving-jobs", type=int, default=24,
+                    help="jobs in the serving stream measured beside the throughput (0: skip)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode comparison run")
     return ap.parse_args()
 
 
@@ -271,6 +274,11 @@ def run_ours(args, rank, ws, local):
     }
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, w, params, g)
+    if rank == 0 and not args.no_fp64 and args.mode != "fp64":
+        out["fp64"] = run_fp64_comparison()
+        out["speedup_vs_fp64"] = value / out["fp64"]["value"]
+    if rank == 0 and args.serving_jobs > 0:
+        out["serving"] = run_serving(args.serving_jobs)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(w, args.cpu_budget_s)
     return out
@@ -326,6 +334,116 @@ def run_cpu_baseline(w, budget_s):
             "cores": int(threads) if threads else (os.cpu_count() or 1), "kind": "oracle",
             "sample": f"first {n} steps of the same N={w.n_traj} job (factorised Heff, same rank)",
             "s_per_step": dt / n}
+
+
+# ---------------------------------------------------------------- FP64 comparison and serving
+
+def run_fp64_comparison(steps=10, warmup=2):
+    """The same workload in FP64 mode (same GB300, same process): trajectory-steps/s."""
+    import torch
+    import paper_1805_11169_gb300 as g
+    prec, dtype_name, cutoff, eps = MODES["fp64"]
+    w = make_workload(1024, cutoff, eps)
+    sim = g.Icwf(g.params_from(w, precision=prec), w.V)
+    sim.init_from_density(w.psi0, w.seed)
+    stream = torch.cuda.ExternalStream(sim.stream())
+    for _ in range(warmup):
+        sim.step(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    k = sim.info()["rank"]
+    sim.close()
+    return {"value": w.n_traj * steps / (ms / 1e3), "unit": "trajectory-steps/s",
+            "ms_per_step": ms / steps, "dtype": dtype_name, "rank_k": k, "steps": steps,
+            "svd_rel_cutoff": cutoff, "s_reg_eps": eps}
+
+
+def _model_library(rng):
+    """A few synthetic model instances (grids and parameters drawn like the mixed-size stream:
+    Shin-Metiu with R_f ~ U[4, 6], R0 ~ U[-5, -3]; cavity with lambda ~ U[0.1, 1])."""
+    from workloads import cavity, shin_metiu
+    lib = []
+    for nx, nR in ((256, 128), (512, 128), (512, 256)):
+        lib.append(shin_metiu(nx=nx, x_range=(-60.0, 60.0), nR=nR, R_range=(-9.0, 9.0),
+                              Rf=float(rng.uniform(4, 6)), R0=float(rng.uniform(-5, -3)),
+                              dt=0.05, n_traj=64, svd_rel_cutoff=1e-8, s_reg_eps=1e-4))
+    for nx, nq in ((512, 128), (1024, 128)):
+        lib.append(cavity(nx=nx, x_range=(-60.0, 60.0), nq=nq, q_range=(-20.0, 20.0),
+                          lam=float(rng.uniform(0.1, 1.0)), dt=0.05, n_traj=64,
+                          svd_rel_cutoff=1e-8, s_reg_eps=1e-4))
+    return lib
+
+
+def run_serving(n_jobs, seed=0, load=0.7, max_live=16):
+    """Poisson stream of mixed-size jobs through the pool (continuous batching): job latency
+    p50/p99 (arrival -> result on the host) and aggregate trajectory-steps/s."""
+    import numpy as np
+    import paper_1805_11169_gb300 as g
+    rng = np.random.default_rng(seed)
+    lib = _model_library(rng)
+    Ns = (64, 128, 256, 512)
+    jobs = []
+    for j in range(n_jobs):
+        jobs.append(dict(model=int(rng.integers(len(lib))), N=int(rng.choice(Ns)),
+                         steps=int(rng.integers(100, 401)), seed=int(rng.integers(1 << 31))))
+
+    def make(job):
+        w = lib[job["model"]].with_(n_traj=job["N"])
+        sim = g.Icwf(g.params_from(w, precision=2), w.V)
+        sim.set_projectors(w.phi)
+        sim.init_from_density(w.psi0, job["seed"])
+        return sim, w
+
+    # isolated service time of the mean job (calibrates the arrival rate to the load factor)
+    t_iso = []
+    for job in jobs[: min(4, n_jobs)]:
+        t0 = time.perf_counter()
+        sim, _ = make(job)
+        sim.step(job["steps"])
+        sim.observables()
+        sim.close()
+        t_iso.append((time.perf_counter() - t0) / job["steps"])
+    mean_service = float(np.mean(t_iso)) * float(np.mean([j["steps"] for j in jobs]))
+    rate = load * max(1.0, max_live / 4) / mean_service
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
+
+    pool = g.icwf_pool_create(64 << 30, max_live)
+    t_start = time.perf_counter()
+    submitted, lat, ids, grids = 0, {}, {}, {}
+    done = set()
+    while len(done) < n_jobs:
+        now = time.perf_counter() - t_start
+        while submitted < n_jobs and arrivals[submitted] <= now:
+            sim, w = make(jobs[submitted])
+            ids[submitted] = g.icwf_pool_submit(pool, sim.release(), jobs[submitted]["steps"])
+            grids[submitted] = (w.nx, w.nR)
+            submitted += 1
+        if submitted == len(done) and submitted < n_jobs:
+            time.sleep(max(0.0, min(0.01, arrivals[submitted] - now)))
+            continue
+        g.icwf_pool_tick(pool)
+        for j, jid in ids.items():
+            if j in done:
+                continue
+            st, _ = g.icwf_pool_poll(pool, jid, *grids[j])
+            if st in (2, 3):
+                done.add(j)
+                lat[j] = time.perf_counter() - t_start - arrivals[j]
+    makespan = time.perf_counter() - t_start
+    g.icwf_pool_destroy(pool)
+    L = np.array([lat[j] for j in range(n_jobs)])
+    ts = sum(j["N"] * j["steps"] for j in jobs)
+    return {"jobs": n_jobs, "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)),
+            "traj_steps_per_s": ts / makespan, "makespan_s": makespan,
+            "arrival_rate_per_s": rate, "max_live": max_live, "precision": "mixed-tf32x3",
+            "stream": "Poisson arrivals; Shin-Metiu (3 grids) and cavity (2 grids) models; "
+                      "N in {64,128,256,512}; 100-400 steps; CI-sized stand-in for 2000 jobs"}
 
 
 # ---------------------------------------------------------------- reference arm (the oracle)

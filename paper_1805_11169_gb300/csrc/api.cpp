@@ -272,20 +272,33 @@ void factor(icwf_ctx* h, int n, const double2* const* S0, const double2* const* 
             const double* theta, double2* const* dst, double* const* inv, double2* const* D) {
   {
     ProfScope ps(h, F_SHIFT);
-    for (int m = 0; m < n; ++m)
-      launch_shift_mix(h->N, S0[m], S1[m], h->p.s_reg_eps, theta[m], dst[m], h->stream);
+    for (int m = 0; m < n; ++m) {
+      if (h->mixed) launch_shift_mix_df(h->N, S0[m], S1[m], h->p.s_reg_eps, theta[m], dst[m], h->stream);
+      else launch_shift_mix(h->N, S0[m], S1[m], h->p.s_reg_eps, theta[m], dst[m], h->stream);
+    }
     h->launches += n;
   }
   ProfScope ps(h, F_POTRF);
-  h->launches += launch_cholesky(h->N, dst, inv, D, n, h->status, h->stream);
+  if (h->mixed) {
+    void* a[2] = {dst[0], n > 1 ? dst[1] : dst[0]};
+    void* iv[2] = {inv[0], n > 1 ? inv[1] : inv[0]};
+    void* dd[2] = {D[0], n > 1 ? D[1] : D[0]};
+    h->launches += launch_cholesky_df(h->N, a, iv, dd, n, h->status, h->stream);
+  } else {
+    h->launches += launch_cholesky(h->N, dst, inv, D, n, h->status, h->stream);
+  }
 }
 
 void solve(icwf_ctx* h, const double2* Lf, const double2* D, const double2* y, double2* out,
            bool minus_i) {
   ProfScope ps(h, F_SOLVE);
   ++h->epoch;
-  launch_chol_solve(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
-                    h->status, h->stream);
+  if (h->mixed)
+    launch_chol_solve_df(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
+                         h->status, h->stream);
+  else
+    launch_chol_solve(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
+                      h->status, h->stream);
   h->launches += 2;
 }
 

@@ -100,6 +100,16 @@ void launch_matvec(int N, const double2* H0, const double2* H1, double theta, co
 void launch_chol_solve(int N, const double2* L, const double2* D, const double2* y, double2* work,
                        double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
                        unsigned epoch, int* status, cudaStream_t s);
+// Mixed modes: the same factorisation and solves in double-float arithmetic (k_linalg_df.cu).
+// A, L and D hold complex double-floats (16 bytes each, the size of a complex128), inv holds
+// double-float reciprocal pivots (8 bytes each); y and out are complex128.
+void launch_shift_mix_df(int N, const double2* S0, const double2* S1, double eps, double theta,
+                         void* A, cudaStream_t s);
+int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, int nbatch,
+                       int* status, cudaStream_t s);
+void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y, void* work,
+                          double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
+                          unsigned epoch, int* status, cudaStream_t s);
 // C += dt/6 (k1 + 2 k2 + 2 k3 + k4); flags non-finite values.
 void launch_rk4_final(int N, double2* C, const double2* k1, const double2* k2,
                       const double2* k3, const double2* k4, double dt, int* status,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "icwf_internal.h"
+#include "df64.cuh"
 #include "k_common.cuh"
 
 namespace icwf {
@@ -45,130 +46,144 @@ void launch_shift_mix(int N, const double2* S0, const double2* S1, double eps, d
 
 struct MatBatch { double2* m[2]; double* inv[2]; double2* D[2]; };
 
-// Factor the diagonal block jb of each matrix: one warp per matrix, lane r holds row r of the
-// block in registers.  Column c: pivot d = A_cc, 1/sqrt(d) by rsqrt, L_cc = d * rsqrt(d);
-// L_rc *= rsqrt(d) for r > c; rank-1 update of the trailing block with column c broadcast by
-// shuffles.  The reciprocal pivots are stored for the panel and triangular solves.  Rows and
-// columns beyond N are treated as identity so that ragged sizes factor cleanly.
-__global__ void __launch_bounds__(32) k_potrf_diag(int N, MatBatch mb, int jb, int* status) {
+constexpr int PF_THREADS = 256;
+
+DF_HD cdf cdf_from(double2 z) { return cdf_make(df_from(z.x), df_from(z.y)); }
+DF_HD double2 cdf_to(cdf z) { return make_double2(df_to(z.re), df_to(z.im)); }
+
+// Factor the diagonal block jb of each matrix (one CTA per matrix).  The 32 x 32 block is
+// converted to double-float (FP32 pairs, ~48 bits) in shared memory, so the column-by-column
+// pivot chain (pivot -> 1/sqrt -> next pivot) runs on FP32 instructions, whose latency is a small
+// fraction of FP64's on this GPU.  Column c: y = 1/sqrt(A_cc) (Newton from an FP32 seed),
+// L_cc = A_cc y; the trailing triangle takes the rank-1 update A_rq -= A_rc conj(A_qc) y^2 from
+// the unscaled column, which is scaled (L_rc = A_rc y) one column later, when nothing reads it
+// any more: two barriers per column.  Outputs (FP64): L in place and the reciprocal pivots.
+// Rows and columns beyond N are treated as identity so that ragged sizes factor cleanly.
+__global__ void __launch_bounds__(PF_THREADS) k_potrf_diag(int N, MatBatch mb, int jb, int* status) {
+  __shared__ cdf L[NB][NB + 1];
+  __shared__ df yv[NB];
+  __shared__ df y2s;
   double2* A = mb.m[blockIdx.y];
   double* inv = mb.inv[blockIdx.y];
-  const int r = threadIdx.x;
   const int r0 = jb * NB;
-  const bool rok = r0 + r < N;
-  double2 L[NB];
-#pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    double2 v = make_double2(c == r ? 1.0 : 0.0, 0.0);
-    if (rok && r0 + c < N && c <= r) v = A[(size_t)(r0 + r) * N + r0 + c];
-    L[c] = v;
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
+  for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
+    const int r = e / NB, c = e % NB;
+    double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    if (c <= r && r0 + r < N && r0 + c < N) v = A[(size_t)(r0 + r) * N + r0 + c];
+    L[r][c] = cdf_from(v);
   }
-  double my_inv = 1.0;
-#pragma unroll
+  __syncthreads();
   for (int c = 0; c < NB; ++c) {
-    double dinv = 0.0;
-    if (r == c) {
-      double d = L[c].x;
-      if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
-      dinv = rsqrt(d);
-      L[c] = make_double2(d * dinv, 0.0);
-      my_inv = dinv;
+    if (threadIdx.x == 0) {
+      df d = L[c][c].re;
+      if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
+      const df y = df_rsqrt(d);
+      L[c][c] = cdf_make(df_mul(d, y), zero);
+      yv[c] = y;
+      y2s = df_mul(y, y);
     }
-    dinv = __shfl_sync(0xffffffffu, dinv, c);
-    if (r > c) L[c] = cscale(L[c], dinv);
-#pragma unroll
-    for (int q = c + 1; q < NB; ++q) {
-      double2 lq;
-      lq.x = __shfl_sync(0xffffffffu, L[c].x, q);
-      lq.y = __shfl_sync(0xffffffffu, L[c].y, q);
-      if (r >= q) {
-        // L[r][q] -= L[r][c] * conj(L[q][c])
-        L[q].x -= L[c].x * lq.x + L[c].y * lq.y;
-        L[q].y -= L[c].y * lq.x - L[c].x * lq.y;
+    __syncthreads();
+    if (c > 0) {
+      // column c-1 is no longer read: scale it now
+      const int r = c + (int)threadIdx.x;
+      if (r < NB) L[r][c - 1] = cdf_scale(L[r][c - 1], yv[c - 1]);
+    }
+    const df y2 = y2s;
+    const int m = NB - 1 - c;
+    for (int e = threadIdx.x; e < m * m; e += PF_THREADS) {
+      const int r = c + 1 + e / m, q = c + 1 + e % m;
+      if (q <= r) {
+        const cdf p = cdf_mul_conj(L[r][c], L[q][c]);
+        L[r][q] = cdf_sub(L[r][q], cdf_scale(p, y2));
       }
     }
+    __syncthreads();
   }
-  if (rok) {
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (c <= r && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = L[c];
-    inv[r0 + r] = my_inv;
+  // column NB-1 has no entries below the diagonal; store
+  for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
+    const int r = e / NB, c = e % NB;
+    if (c <= r && r0 + r < N && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = cdf_to(L[r][c]);
   }
+  if (threadIdx.x < NB && r0 + threadIdx.x < N) inv[r0 + threadIdx.x] = df_to(yv[threadIdx.x]);
 }
 
 constexpr int TR_WARPS = 8;   // rows per panel-solve CTA
 
-// Panel solve A_ib <- A_ib L_bb^-H below the diagonal block jb: one warp per row, lane = column.
-// Column-oriented substitution: x_m = a_m / L_mm, then a_c -= x_m conj(L_cm) for c > m.
+// Panel solve A_ib <- A_ib L_bb^-H below the diagonal block jb: one warp per row, lane = column,
+// column-oriented substitution x_m = a_m / L_mm, a_c -= x_m conj(L_cm) (c > m) in double-float,
+// so that the 32-step chain runs on FP32 latencies.  Inputs and outputs are FP64.
 __global__ void __launch_bounds__(TR_WARPS * 32) k_trsm_panel(int N, MatBatch mb, int jb) {
-  __shared__ double2 Ls[NB][NB + 1];
-  __shared__ double invs[NB];
+  __shared__ cdf Ls[NB][NB + 1];
+  __shared__ df ys[NB];
   double2* A = mb.m[blockIdx.y];
   const double* inv = mb.inv[blockIdx.y];
   const int c0 = jb * NB;
+  const df zero = df_make(0.f, 0.f);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
     double2 l = make_double2(0.0, 0.0);
     if (c < r && c0 + r < N && c0 + c < N) l = A[(size_t)(c0 + r) * N + c0 + c];
-    Ls[r][c] = l;
+    Ls[r][c] = cdf_from(l);
   }
-  if (threadIdx.x < NB) invs[threadIdx.x] = (c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : 1.0;
+  if (threadIdx.x < NB) ys[threadIdx.x] = df_from((c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : 1.0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = (jb + 1) * NB + blockIdx.x * TR_WARPS + warp;
   if (row >= N) return;
   const bool cok = c0 + lane < N;
-  double2 a = cok ? A[(size_t)row * N + c0 + lane] : make_double2(0.0, 0.0);
-#pragma unroll
+  cdf a = cdf_from(cok ? A[(size_t)row * N + c0 + lane] : make_double2(0.0, 0.0));
+#pragma unroll 4
   for (int m = 0; m < NB; ++m) {
-    double2 x = cscale(a, invs[m]);
-    x.x = __shfl_sync(0xffffffffu, x.x, m);
-    x.y = __shfl_sync(0xffffffffu, x.y, m);
+    const cdf xs = cdf_scale(a, ys[m]);
+    cdf x;
+    x.re.h = __shfl_sync(0xffffffffu, xs.re.h, m);
+    x.re.l = __shfl_sync(0xffffffffu, xs.re.l, m);
+    x.im.h = __shfl_sync(0xffffffffu, xs.im.h, m);
+    x.im.l = __shfl_sync(0xffffffffu, xs.im.l, m);
     if (lane == m) a = x;
-    else if (lane > m) {
-      const double2 l = Ls[lane][m];
-      a.x -= x.x * l.x + x.y * l.y;   // a -= x conj(l)
-      a.y -= x.y * l.x - x.x * l.y;
-    }
+    else if (lane > m) a = cdf_sub(a, cdf_mul_conj(x, Ls[lane][m]));
   }
-  if (cok) A[(size_t)row * N + c0 + lane] = a;
+  (void)zero;
+  if (cok) A[(size_t)row * N + c0 + lane] = cdf_to(a);
 }
 
-// Inverse of every diagonal block after the factorisation: D_b = L_bb^-1 (lower triangular,
-// 32 x 32), stored row-major per block in D[(b*32 + r)*32 + c].  One warp per block, lane = column
-// c of D: D_rc = (delta_rc - sum_{c<=m<r} L_rm D_mc) / L_rr for r >= c.  The triangular solves use
-// these blocks as matrix-vector products, which keeps the dependent substitution chain off their
-// critical path.
-__global__ void __launch_bounds__(32) k_trtri_diag(int N, MatBatch mb) {
-  __shared__ double2 Ls[NB][NB + 1];
-  __shared__ double invs[NB];
+// Inverse of every diagonal block after the factorisation: D_b = L_bb^-1 (lower triangular),
+// row-major per block in D[(b*32 + r)*32 + c], one CTA per block, all blocks at once.
+// Right-looking elimination in double-float: for k = 0..31, row k of D is scaled by 1/L_kk (it is
+// then final) and removed from the rows below with the multipliers L_rk.
+__global__ void __launch_bounds__(128) k_trtri_diag(int N, MatBatch mb) {
+  __shared__ cdf Ls[NB][NB + 1];
+  __shared__ cdf Dm[NB][NB + 1];
+  __shared__ df ys[NB];
   const double2* A = mb.m[blockIdx.y];
   const double* inv = mb.inv[blockIdx.y];
   double2* D = mb.D[blockIdx.y];
-  const int jb = blockIdx.x, r0 = jb * NB, c = threadIdx.x;
-  for (int r = 0; r < NB; ++r) {
-    double2 l = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  const int jb = blockIdx.x, r0 = jb * NB;
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    double2 l = make_double2(0.0, 0.0);
     if (c < r && r0 + r < N && r0 + c < N) l = A[(size_t)(r0 + r) * N + r0 + c];
-    Ls[r][c] = l;
+    Ls[r][c] = cdf_from(l);
+    Dm[r][c] = cdf_make(r == c ? one : zero, zero);
   }
-  invs[c] = (r0 + c < N) ? inv[r0 + c] : 1.0;
-  __syncwarp();
-  double2 d[NB];
-#pragma unroll
-  for (int r = 0; r < NB; ++r) {
-    double2 acc = make_double2(r == c ? 1.0 : 0.0, 0.0);
-#pragma unroll
-    for (int m = 0; m < r; ++m) {
-      // only m >= c contributes (D_mc = 0 for m < c); the loop stays uniform across lanes
-      const double2 l = Ls[r][m];
-      acc.x -= l.x * d[m].x - l.y * d[m].y;
-      acc.y -= l.x * d[m].y + l.y * d[m].x;
+  if (threadIdx.x < NB) ys[threadIdx.x] = df_from((r0 + threadIdx.x < N) ? inv[r0 + threadIdx.x] : 1.0);
+  __syncthreads();
+  for (int k = 0; k < NB; ++k) {
+    if (threadIdx.x <= k) Dm[k][threadIdx.x] = cdf_scale(Dm[k][threadIdx.x], ys[k]);
+    __syncthreads();
+    const int rows = NB - 1 - k, cols = k + 1;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int r = k + 1 + e / cols, c = e % cols;
+      Dm[r][c] = cdf_sub(Dm[r][c], cdf_mul(Ls[r][k], Dm[k][c]));
     }
-    d[r] = (r >= c) ? cscale(acc, invs[r]) : make_double2(0.0, 0.0);
+    __syncthreads();
   }
-#pragma unroll
-  for (int r = 0; r < NB; ++r)
-    if (r0 + r < N) D[((size_t)jb * NB + r) * NB + c] = d[r];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    if (r0 + r < N) D[((size_t)jb * NB + r) * NB + c] = cdf_to(Dm[r][c]);
+  }
 }
 
 __device__ __forceinline__ void tri_index_l(int t, int& I, int& J) {
@@ -200,13 +215,28 @@ __global__ void __launch_bounds__(256) k_herk_update(int N, MatBatch mb, int jb)
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const double2 z = make_double2(0, 0);
   double2 acc[2][2] = {{z, z}, {z, z}};
-#pragma unroll 8
-  for (int m = 0; m < NB; ++m) {
-    const double2 a0 = Lr[ty][m], a1 = Lr[ty + 16][m];
-    const double2 b0 = Lc[tx][m], b1 = Lc[tx + 16][m];
-    // acc += a * conj(b)
-    cfmac(acc[0][0], b0, a0); cfmac(acc[0][1], b1, a0);
-    cfmac(acc[1][0], b0, a1); cfmac(acc[1][1], b1, a1);
+  {
+    // four independent partial sums per output (FP64 latency), combined at the end
+    double2 pa[4][2][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) pa[q][r][c] = z;
+#pragma unroll
+    for (int m = 0; m < NB; ++m) {
+      const double2 a0 = Lr[ty][m], a1 = Lr[ty + 16][m];
+      const double2 b0 = Lc[tx][m], b1 = Lc[tx + 16][m];
+      // acc += a * conj(b)
+      cfmac(pa[m & 3][0][0], b0, a0); cfmac(pa[m & 3][0][1], b1, a0);
+      cfmac(pa[m & 3][1][0], b0, a1); cfmac(pa[m & 3][1][1], b1, a1);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+        acc[r][c] = cadd(cadd(pa[0][r][c], pa[1][r][c]), cadd(pa[2][r][c], pa[3][r][c]));
   }
 #pragma unroll
   for (int r = 0; r < 2; ++r)
@@ -234,7 +264,7 @@ int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const
   const int T = (N + NB - 1) / NB;
   int launches = 0;
   for (int jb = 0; jb < T; ++jb) {
-    k_potrf_diag<<<dim3(1, nbatch), 32, 0, s>>>(N, mb, jb, status);
+    k_potrf_diag<<<dim3(1, nbatch), PF_THREADS, 0, s>>>(N, mb, jb, status);
     ++launches;
     const int rest = T - jb - 1;
     if (rest > 0) {
@@ -244,7 +274,7 @@ int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const
       launches += 2;
     }
   }
-  k_trtri_diag<<<dim3(T, nbatch), 32, 0, s>>>(N, mb);
+  k_trtri_diag<<<dim3(T, nbatch), 128, 0, s>>>(N, mb);
   return launches + 1;
 }
 
@@ -296,6 +326,25 @@ __device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned epoch, int
 }
 
 constexpr int TW = 8;   // warps per triangular-solve CTA
+constexpr int CW = 4;   // warps sharing the critical block and the diagonal product (one per SM
+                        // sub-partition, so the FP64 work on the dependency chain uses all four
+                        // FP64 units of the SM)
+
+// Dependent FP64 operations are very slow on this part (hundreds of cycles of latency), so the
+// short complex dot products on the solves' dependency chain are evaluated as independent
+// products followed by a pairwise tree, never as one running accumulator.
+template <int K>
+__device__ __forceinline__ double2 tree_sum(double2 (&t)[K]) {
+#pragma unroll
+  for (int w = 1; w < K; w *= 2)
+#pragma unroll
+    for (int q = 0; q + w < K; q += 2 * w) t[q] = cadd(t[q], t[q + w]);
+  return t[0];
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
@@ -313,6 +362,7 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_lower(int N, const double2* __
                                                        int* status) {
   __shared__ double2 part[TW][NB];
   __shared__ double2 Ds[NB][NB + 1];
+  __shared__ double2 vsh[NB];
   __shared__ int s_jb;
   if (threadIdx.x == 0) s_jb = (int)atomicAdd(ticket, 1u);
   __syncthreads();
@@ -326,64 +376,95 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_lower(int N, const double2* __
   const bool row_ok = r0 + lane < N;
   const double2* Lrow = L + (size_t)(row_ok ? r0 + lane : 0) * N;
   double2 acc = make_double2(0, 0);
-  // warps 1..TW-1: blocks m = 0 .. jb-2, round robin
-  for (int m = warp - 1; warp > 0 && m < jb - 1; m += TW - 1) {
+  // warps CW..TW-1: blocks m = 0 .. jb-2, round robin (the critical warps 0..CW-1 take jb-1)
+  for (int m = warp - CW; warp >= CW && m < jb - 1; m += TW - CW) {
     double2 lv[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) lv[c] = __ldg(Lrow + m * NB + c);
     if (lane == 0) wait_flag(flags + m, epoch, status);
     __syncwarp();
     const double2 zm = __ldcg(z + m * NB + lane);
+    double2 t[4] = {acc, make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       double2 zc;
       zc.x = __shfl_sync(0xffffffffu, zm.x, c);
       zc.y = __shfl_sync(0xffffffffu, zm.y, c);
-      cfma(acc, lv[c], zc);
+      cfma(t[c & 3], lv[c], zc);
     }
+    acc = tree_sum(t);
   }
-  if (warp > 0) part[warp][lane] = row_ok ? acc : make_double2(0, 0);
-  __syncthreads();
-  if (warp != 0) return;
-  // warp 0: prefetch the critical block (jb-1), then wait for z_{jb-1}
-  double2 lv[NB];
+  if (warp >= CW) part[warp][lane] = row_ok ? acc : make_double2(0, 0);
+  // warps 0..CW-1 prefetch their columns of the critical block (jb-1)
   const int mc = jb - 1;
+  constexpr int CPW = NB / CW;   // columns per critical warp
+  double2 lv[CPW];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) lv[c] = (mc >= 0) ? __ldg(Lrow + mc * NB + c) : make_double2(0, 0);
-  double2 v = row_ok ? y[r0 + lane] : make_double2(0, 0);
-  for (int w = 1; w < TW; ++w) v = csub(v, part[w][lane]);
+  for (int q = 0; q < CPW; ++q)
+    lv[q] = (warp < CW && mc >= 0) ? __ldg(Lrow + mc * NB + warp * CPW + q) : make_double2(0, 0);
+  __syncthreads();   // part[] of warps CW.. complete
+  if (warp >= CW) return;
+  double2 v = make_double2(0, 0);
+  if (warp == 0) {
+    v = row_ok ? y[r0 + lane] : make_double2(0, 0);
+    for (int w = CW; w < TW; ++w) v = csub(v, part[w][lane]);
+  }
+  double2 p = make_double2(0, 0);
   if (mc >= 0) {
     if (lane == 0) wait_flag(flags + mc, epoch, status);
     __syncwarp();
     const double2 zm = __ldcg(z + mc * NB + lane);
-    double2 p = make_double2(0, 0);
+    double2 t[CPW];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp * CPW + q;
       double2 zc;
       zc.x = __shfl_sync(0xffffffffu, zm.x, c);
       zc.y = __shfl_sync(0xffffffffu, zm.y, c);
-      cfma(p, lv[c], zc);
+      t[q] = cmul(lv[q], zc);
     }
-    if (row_ok) v = csub(v, p);
+    p = tree_sum(t);
   }
-  // z_jb = D_jb v
-  double2 out = make_double2(0, 0);
+  part[warp][lane] = p;   // rows' partial products, one per critical warp
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    double2 t[CW];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    double2 vc;
-    vc.x = __shfl_sync(0xffffffffu, v.x, c);
-    vc.y = __shfl_sync(0xffffffffu, v.y, c);
-    cfma(out, Ds[lane][c], vc);
+    for (int w = 0; w < CW; ++w) t[w] = part[w][lane];
+    v = csub(v, tree_sum(t));
+    if (!row_ok) v = make_double2(0, 0);
+    vsh[lane] = v;
   }
-  if (row_ok) z[r0 + lane] = out;
-  fence_acq_rel_gpu();
-  __syncwarp();
-  if (lane == 0) st_release(flags + jb, epoch);
+  named_sync(1, CW * 32);
+  // z_jb = D_jb v, columns split over the critical warps
+  double2 out;
+  {
+    double2 t[CPW];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp * CPW + q;
+      t[q] = cmul(Ds[lane][c], vsh[c]);
+    }
+    out = tree_sum(t);
+  }
+  part[warp][lane] = out;
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    double2 t[CW];
+#pragma unroll
+    for (int w = 0; w < CW; ++w) t[w] = part[w][lane];
+    const double2 zz = tree_sum(t);
+    if (row_ok) z[r0 + lane] = zz;
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) st_release(flags + jb, epoch);
+  }
 }
 
 // Backward solve L^H w = z, block rows in reverse ticket order:
 //   w_b = D_b^H (z_b - sum_{m>b} L_mb^H w_m);  out = w or -i w.
-// Lane r of a warp reads column r0 + r of the block rows below (coalesced across lanes).
+// Lane r of a warp reads column r0 + r of the block rows below (coalesced across lanes).  Warps
+// 0..CW-1 share the critical block (jb+1) and the diagonal product; the others take the rest.
 __global__ void __launch_bounds__(TW * 32) k_trsv_upper(int N, const double2* __restrict__ L,
                                                        const double2* __restrict__ D,
                                                        const double2* __restrict__ z,
@@ -393,6 +474,7 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_upper(int N, const double2* __
                                                        int* status) {
   __shared__ double2 part[TW][NB];
   __shared__ double2 Ds[NB][NB + 1];
+  __shared__ double2 vsh[NB];
   __shared__ int s_jb;
   const int nblk = (N + NB - 1) / NB;
   if (threadIdx.x == 0) s_jb = nblk - 1 - (int)atomicAdd(ticket, 1u);
@@ -406,8 +488,8 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_upper(int N, const double2* __
   }
   const bool col_ok = r0 + lane < N;
   double2 acc = make_double2(0, 0);
-  // warps 1..TW-1: blocks m = jb+2 .. nblk-1
-  for (int m = jb + 2 + (warp - 1); warp > 0 && m < nblk; m += TW - 1) {
+  // warps CW..TW-1: blocks m = nblk-1 .. jb+2, in the order the blocks complete (descending)
+  for (int m = nblk - 1 - (warp - CW); warp >= CW && m >= jb + 2; m -= TW - CW) {
     double2 lv[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
@@ -418,57 +500,88 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_upper(int N, const double2* __
     if (lane == 0) wait_flag(flags + m, epoch, status);
     __syncwarp();
     const double2 wm = (m * NB + lane < N) ? __ldcg(wbuf + m * NB + lane) : make_double2(0, 0);
+    double2 t[4] = {acc, make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       double2 wc;
       wc.x = __shfl_sync(0xffffffffu, wm.x, c);
       wc.y = __shfl_sync(0xffffffffu, wm.y, c);
-      cfmac(acc, lv[c], wc);
+      cfmac(t[c & 3], lv[c], wc);
     }
+    acc = tree_sum(t);
   }
-  if (warp > 0) part[warp][lane] = acc;
-  __syncthreads();
-  if (warp != 0) return;
+  if (warp >= CW) part[warp][lane] = acc;
   const int mc = jb + 1;
-  double2 lv[NB];
+  constexpr int CPW = NB / CW;
+  double2 lv[CPW];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) {
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp * CPW + q;
     double2 l = make_double2(0, 0);
-    if (mc < nblk && mc * NB + c < N && col_ok) l = __ldg(L + (size_t)(mc * NB + c) * N + r0 + lane);
-    lv[c] = l;
+    if (warp < CW && mc < nblk && mc * NB + c < N && col_ok)
+      l = __ldg(L + (size_t)(mc * NB + c) * N + r0 + lane);
+    lv[q] = l;
   }
-  double2 v = col_ok ? z[r0 + lane] : make_double2(0, 0);
-  for (int w = 1; w < TW; ++w) v = csub(v, part[w][lane]);
+  __syncthreads();
+  if (warp >= CW) return;
+  double2 v = make_double2(0, 0);
+  if (warp == 0) {
+    v = col_ok ? z[r0 + lane] : make_double2(0, 0);
+    for (int w = CW; w < TW; ++w) v = csub(v, part[w][lane]);
+  }
+  double2 p = make_double2(0, 0);
   if (mc < nblk) {
     if (lane == 0) wait_flag(flags + mc, epoch, status);
     __syncwarp();
     const double2 wm = (mc * NB + lane < N) ? __ldcg(wbuf + mc * NB + lane) : make_double2(0, 0);
-    double2 p = make_double2(0, 0);
+    double2 t[CPW];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp * CPW + q;
       double2 wc;
       wc.x = __shfl_sync(0xffffffffu, wm.x, c);
       wc.y = __shfl_sync(0xffffffffu, wm.y, c);
-      cfmac(p, lv[c], wc);
+      t[q] = cmulc(lv[q], wc);
     }
-    v = csub(v, p);
+    p = tree_sum(t);
   }
-  // w_jb = D_jb^H v: w_r = sum_c conj(D_cr) v_c
-  double2 out = make_double2(0, 0);
+  part[warp][lane] = p;
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    double2 t[CW];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    double2 vc;
-    vc.x = __shfl_sync(0xffffffffu, v.x, c);
-    vc.y = __shfl_sync(0xffffffffu, v.y, c);
-    cfmac(out, Ds[c][lane], vc);
+    for (int w = 0; w < CW; ++w) t[w] = part[w][lane];
+    v = csub(v, tree_sum(t));
+    if (!col_ok) v = make_double2(0, 0);
+    vsh[lane] = v;
   }
-  if (col_ok) {
-    wbuf[r0 + lane] = out;
-    w_out[r0 + lane] = minus_i ? make_double2(out.y, -out.x) : out;
+  named_sync(1, CW * 32);
+  // w_jb = D_jb^H v: w_r = sum_c conj(D_cr) v_c, columns split over the critical warps
+  double2 out;
+  {
+    double2 t[CPW];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp * CPW + q;
+      t[q] = cmulc(Ds[c][lane], vsh[c]);
+    }
+    out = tree_sum(t);
   }
-  fence_acq_rel_gpu();
-  __syncwarp();
-  if (lane == 0) st_release(flags + jb, epoch);
+  part[warp][lane] = out;
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    double2 t[CW];
+#pragma unroll
+    for (int w = 0; w < CW; ++w) t[w] = part[w][lane];
+    const double2 ww = tree_sum(t);
+    if (col_ok) {
+      wbuf[r0 + lane] = ww;
+      w_out[r0 + lane] = minus_i ? make_double2(ww.y, -ww.x) : ww;
+    }
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) st_release(flags + jb, epoch);
+  }
 }
 
 void launch_chol_solve(int N, const double2* L, const double2* D, const double2* y, double2* work,

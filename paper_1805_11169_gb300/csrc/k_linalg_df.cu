@@ -1,0 +1,553 @@
+// Coefficient solve of the mixed-precision modes (Eq. coeff) in double-float arithmetic.
+//
+// The regularised overlap S + eps I is factorised and the RK4 stage systems are solved with
+// complex numbers stored as (re_hi, re_lo, im_hi, im_lo) FP32 quadruples (16 bytes, the size of a
+// complex128), each part a double-float of ~48 significant bits (csrc/df64.cuh).  On this GPU the
+// FP32 pipes have ~64x the FP64 throughput and a far shorter latency, and the Cholesky chain and
+// the triangular-solve chains are latency-bound; S itself carries ~1e-6 relative rounding noise in
+// these modes, far above the 48-bit arithmetic.  Dot products use compensated accumulation in the
+// style of Ogita, Rump and Oishi's Dot2 (TwoProduct + TwoSum, errors summed separately), which
+// returns them as accurately as if evaluated in twice the FP32 precision.
+//
+// Kernels mirror the FP64 ones in k_linalg.cu: shift (S -> S + eps I, converted), diagonal factor,
+// panel solve, trailing update, diagonal-block inverses, forward / backward triangular solves.
+#include <cuda_runtime.h>
+
+#include "df64.cuh"
+#include "icwf_internal.h"
+#include "k_common.cuh"
+
+namespace icwf {
+namespace dfs {
+
+constexpr int NB = 32;
+constexpr unsigned WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ cdf ld4(const float4 v) {
+  return cdf_make(df_make(v.x, v.y), df_make(v.z, v.w));
+}
+__device__ __forceinline__ float4 st4(cdf z) { return make_float4(z.re.h, z.re.l, z.im.h, z.im.l); }
+__device__ __forceinline__ cdf czero() { return cdf_make(df_make(0.f, 0.f), df_make(0.f, 0.f)); }
+
+// Compensated accumulator: value = s + c.
+struct acc2 {
+  float s, c;
+};
+__device__ __forceinline__ void acc_prod(acc2& a, float x, float y) {
+  const float p = DF_MUL(x, y);
+  const float e = DF_FMA(x, y, -p);
+  const df t = two_sum(a.s, p);
+  a.s = t.h;
+  a.c = DF_ADD(a.c, DF_ADD(t.l, e));
+}
+__device__ __forceinline__ void acc_small(acc2& a, float x) { a.c = DF_ADD(a.c, x); }
+__device__ __forceinline__ df acc_val(acc2 a) { return two_sum(a.s, a.c); }
+__device__ __forceinline__ acc2 acc_zero() { acc2 a; a.s = 0.f; a.c = 0.f; return a; }
+__device__ __forceinline__ acc2 acc_merge(acc2 a, acc2 b) {
+  const df t = two_sum(a.s, b.s);
+  acc2 r;
+  r.s = t.h;
+  r.c = DF_ADD(DF_ADD(a.c, b.c), t.l);
+  return r;
+}
+
+struct cacc {
+  acc2 re, im;
+};
+__device__ __forceinline__ cacc cacc_zero() { cacc z; z.re = acc_zero(); z.im = acc_zero(); return z; }
+__device__ __forceinline__ cacc cacc_merge(cacc a, cacc b) {
+  cacc r; r.re = acc_merge(a.re, b.re); r.im = acc_merge(a.im, b.im); return r;
+}
+__device__ __forceinline__ cdf cacc_val(cacc a) { return cdf_make(acc_val(a.re), acc_val(a.im)); }
+// a += x * y
+__device__ __forceinline__ void cacc_mul(cacc& a, cdf x, cdf y) {
+  acc_prod(a.re, x.re.h, y.re.h);
+  acc_prod(a.re, -x.im.h, y.im.h);
+  acc_small(a.re, DF_FMA(x.re.h, y.re.l, DF_MUL(x.re.l, y.re.h)));
+  acc_small(a.re, -DF_FMA(x.im.h, y.im.l, DF_MUL(x.im.l, y.im.h)));
+  acc_prod(a.im, x.re.h, y.im.h);
+  acc_prod(a.im, x.im.h, y.re.h);
+  acc_small(a.im, DF_FMA(x.re.h, y.im.l, DF_MUL(x.re.l, y.im.h)));
+  acc_small(a.im, DF_FMA(x.im.h, y.re.l, DF_MUL(x.im.l, y.re.h)));
+}
+// a += x * conj(y)
+__device__ __forceinline__ void cacc_mulc(cacc& a, cdf x, cdf y) {
+  acc_prod(a.re, x.re.h, y.re.h);
+  acc_prod(a.re, x.im.h, y.im.h);
+  acc_small(a.re, DF_FMA(x.re.h, y.re.l, DF_MUL(x.re.l, y.re.h)));
+  acc_small(a.re, DF_FMA(x.im.h, y.im.l, DF_MUL(x.im.l, y.im.h)));
+  acc_prod(a.im, x.im.h, y.re.h);
+  acc_prod(a.im, -x.re.h, y.im.h);
+  acc_small(a.im, DF_FMA(x.im.h, y.re.l, DF_MUL(x.im.l, y.re.h)));
+  acc_small(a.im, -DF_FMA(x.re.h, y.im.l, DF_MUL(x.re.l, y.im.h)));
+}
+// a += conj(x) * y
+__device__ __forceinline__ void cacc_cmul(cacc& a, cdf x, cdf y) {
+  acc_prod(a.re, x.re.h, y.re.h);
+  acc_prod(a.re, x.im.h, y.im.h);
+  acc_small(a.re, DF_FMA(x.re.h, y.re.l, DF_MUL(x.re.l, y.re.h)));
+  acc_small(a.re, DF_FMA(x.im.h, y.im.l, DF_MUL(x.im.l, y.im.h)));
+  acc_prod(a.im, x.re.h, y.im.h);
+  acc_prod(a.im, -x.im.h, y.re.h);
+  acc_small(a.im, DF_FMA(x.re.h, y.im.l, DF_MUL(x.re.l, y.im.h)));
+  acc_small(a.im, -DF_FMA(x.im.h, y.re.l, DF_MUL(x.im.l, y.re.h)));
+}
+
+struct Batch {
+  float4* m[2];
+  float2* inv[2];   // 1/L_cc as double-floats
+  float4* D[2];     // inverted diagonal blocks
+};
+
+// ---------------------------------------------------------------------------- S + eps I
+
+__global__ void k_shift_mix_df(int N, const double2* __restrict__ S0, const double2* __restrict__ S1,
+                               double eps, double theta, float4* __restrict__ A) {
+  const size_t NN = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < NN;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e / N, c = e % N;
+    double2 v;
+    if (theta == 1.0) v = S1[e];
+    else if (theta == 0.0) v = S0[e];
+    else v = make_double2(0.5 * (S0[e].x + S1[e].x), 0.5 * (S0[e].y + S1[e].y));
+    if (r == c) v.x += eps;
+    A[e] = st4(cdf_make(df_from(v.x), df_from(v.y)));
+  }
+}
+
+// ---------------------------------------------------------------------------- diagonal factor
+
+constexpr int PF_THREADS = 256;
+
+// Same algorithm as the FP64-storage diagonal factor: double-float pivot chain, rank-1 updates
+// with y^2 from the unscaled column, column scaling one column later.
+__global__ void __launch_bounds__(PF_THREADS) k_potrf_df(int N, Batch mb, int jb, int* status) {
+  __shared__ cdf L[NB][NB + 1];
+  __shared__ df yv[NB];
+  __shared__ df y2s;
+  float4* A = mb.m[blockIdx.y];
+  float2* inv = mb.inv[blockIdx.y];
+  const int r0 = jb * NB;
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
+  for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
+    const int r = e / NB, c = e % NB;
+    cdf v = cdf_make(r == c ? one : zero, zero);
+    if (c <= r && r0 + r < N && r0 + c < N) v = ld4(A[(size_t)(r0 + r) * N + r0 + c]);
+    L[r][c] = v;
+  }
+  __syncthreads();
+  for (int c = 0; c < NB; ++c) {
+    if (threadIdx.x == 0) {
+      df d = L[c][c].re;
+      if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
+      const df y = df_rsqrt(d);
+      L[c][c] = cdf_make(df_mul(d, y), zero);
+      yv[c] = y;
+      y2s = df_mul(y, y);
+    }
+    __syncthreads();
+    if (c > 0) {
+      const int r = c + (int)threadIdx.x;
+      if (r < NB) L[r][c - 1] = cdf_scale(L[r][c - 1], yv[c - 1]);
+    }
+    const df y2 = y2s;
+    const int m = NB - 1 - c;
+    for (int e = threadIdx.x; e < m * m; e += PF_THREADS) {
+      const int r = c + 1 + e / m, q = c + 1 + e % m;
+      if (q <= r) L[r][q] = cdf_sub(L[r][q], cdf_scale(cdf_mul_conj(L[r][c], L[q][c]), y2));
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
+    const int r = e / NB, c = e % NB;
+    if (c <= r && r0 + r < N && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = st4(L[r][c]);
+  }
+  if (threadIdx.x < NB && r0 + threadIdx.x < N)
+    inv[r0 + threadIdx.x] = make_float2(yv[threadIdx.x].h, yv[threadIdx.x].l);
+}
+
+// ---------------------------------------------------------------------------- panel solve
+
+constexpr int TR_WARPS = 8;
+
+__global__ void __launch_bounds__(TR_WARPS * 32) k_trsm_df(int N, Batch mb, int jb) {
+  __shared__ cdf Ls[NB][NB + 1];
+  __shared__ df ys[NB];
+  float4* A = mb.m[blockIdx.y];
+  const float2* inv = mb.inv[blockIdx.y];
+  const int c0 = jb * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    cdf l = czero();
+    if (c < r && c0 + r < N && c0 + c < N) l = ld4(A[(size_t)(c0 + r) * N + c0 + c]);
+    Ls[r][c] = l;
+  }
+  if (threadIdx.x < NB) {
+    const float2 v = (c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : make_float2(1.f, 0.f);
+    ys[threadIdx.x] = df_make(v.x, v.y);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = (jb + 1) * NB + blockIdx.x * TR_WARPS + warp;
+  if (row >= N) return;
+  const bool cok = c0 + lane < N;
+  cdf a = cok ? ld4(A[(size_t)row * N + c0 + lane]) : czero();
+#pragma unroll 4
+  for (int m = 0; m < NB; ++m) {
+    const cdf xs = cdf_scale(a, ys[m]);
+    cdf x;
+    x.re.h = __shfl_sync(0xffffffffu, xs.re.h, m);
+    x.re.l = __shfl_sync(0xffffffffu, xs.re.l, m);
+    x.im.h = __shfl_sync(0xffffffffu, xs.im.h, m);
+    x.im.l = __shfl_sync(0xffffffffu, xs.im.l, m);
+    if (lane == m) a = x;
+    else if (lane > m) a = cdf_sub(a, cdf_mul_conj(x, Ls[lane][m]));
+  }
+  if (cok) A[(size_t)row * N + c0 + lane] = st4(a);
+}
+
+// ---------------------------------------------------------------------------- trailing update
+
+__device__ __forceinline__ void tri_index(int t, int& I, int& J) {
+  int Jc = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (Jc * (Jc + 1) / 2 > t) --Jc;
+  while ((Jc + 1) * (Jc + 2) / 2 <= t) ++Jc;
+  J = Jc;
+  I = t - Jc * (Jc + 1) / 2;
+}
+
+// A_rc -= L_rb L_cb^H for jb < c <= r; compensated dot products of length 32 on the FP32 pipes.
+__global__ void __launch_bounds__(256) k_herk_df(int N, Batch mb, int jb) {
+  __shared__ cdf Lr[NB][NB + 1];
+  __shared__ cdf Lc[NB][NB + 1];
+  float4* A = mb.m[blockIdx.y];
+  int I, J;
+  tri_index(blockIdx.x, I, J);
+  const int cb = jb + 1 + I, rb = jb + 1 + J;
+  const int k0 = jb * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, m = e % NB;
+    cdf a = czero(), b = czero();
+    if (rb * NB + r < N && k0 + m < N) a = ld4(A[(size_t)(rb * NB + r) * N + k0 + m]);
+    if (cb * NB + r < N && k0 + m < N) b = ld4(A[(size_t)(cb * NB + r) * N + k0 + m]);
+    Lr[r][m] = a;
+    Lc[r][m] = b;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cacc acc[2][2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) acc[r][c] = cacc_zero();
+#pragma unroll 4
+  for (int m = 0; m < NB; ++m) {
+    const cdf a0 = Lr[ty][m], a1 = Lr[ty + 16][m];
+    const cdf b0 = Lc[tx][m], b1 = Lc[tx + 16][m];
+    cacc_mulc(acc[0][0], a0, b0);
+    cacc_mulc(acc[0][1], a0, b1);
+    cacc_mulc(acc[1][0], a1, b0);
+    cacc_mulc(acc[1][1], a1, b1);
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int gr = rb * NB + ty + 16 * r, gc = cb * NB + tx + 16 * c;
+      if (gr < N && gc < N && gc <= gr) {
+        float4* p = A + (size_t)gr * N + gc;
+        *p = st4(cdf_sub(ld4(*p), cacc_val(acc[r][c])));
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------- diagonal inverses
+
+__global__ void __launch_bounds__(128) k_trtri_df(int N, Batch mb) {
+  __shared__ cdf Ls[NB][NB + 1];
+  __shared__ cdf Dm[NB][NB + 1];
+  __shared__ df ys[NB];
+  const float4* A = mb.m[blockIdx.y];
+  const float2* inv = mb.inv[blockIdx.y];
+  float4* D = mb.D[blockIdx.y];
+  const int jb = blockIdx.x, r0 = jb * NB;
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    cdf l = czero();
+    if (c < r && r0 + r < N && r0 + c < N) l = ld4(A[(size_t)(r0 + r) * N + r0 + c]);
+    Ls[r][c] = l;
+    Dm[r][c] = cdf_make(r == c ? one : zero, zero);
+  }
+  if (threadIdx.x < NB) {
+    const float2 v = (r0 + threadIdx.x < N) ? inv[r0 + threadIdx.x] : make_float2(1.f, 0.f);
+    ys[threadIdx.x] = df_make(v.x, v.y);
+  }
+  __syncthreads();
+  for (int k = 0; k < NB; ++k) {
+    if (threadIdx.x <= k) Dm[k][threadIdx.x] = cdf_scale(Dm[k][threadIdx.x], ys[k]);
+    __syncthreads();
+    const int rows = NB - 1 - k, cols = k + 1;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int r = k + 1 + e / cols, c = e % cols;
+      Dm[r][c] = cdf_sub(Dm[r][c], cdf_mul(Ls[r][k], Dm[k][c]));
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    if (r0 + r < N) D[((size_t)jb * NB + r) * NB + c] = st4(Dm[r][c]);
+  }
+}
+
+// ---------------------------------------------------------------------------- triangular solves
+
+constexpr int TW = 8;
+constexpr int CW = 4;
+constexpr int CPW = NB / CW;
+
+__device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned epoch, int* status) {
+  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+    if (ld_acquire(f) == epoch) return true;
+    if (it > 4096) __nanosleep(64);
+  }
+  set_flag(status, ST_TIMEOUT);
+  return false;
+}
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
+  cdf r;
+  r.re.h = __shfl_sync(0xffffffffu, v.re.h, src);
+  r.re.l = __shfl_sync(0xffffffffu, v.re.l, src);
+  r.im.h = __shfl_sync(0xffffffffu, v.im.h, src);
+  r.im.l = __shfl_sync(0xffffffffu, v.im.l, src);
+  return r;
+}
+__device__ __forceinline__ cdf ldcg4(const float4* p) { return ld4(__ldcg(p)); }
+
+// Forward solve L z = y (z published as double-floats, consumers wait on per-block flags).
+// Same schedule as the FP64 kernel: warps CW.. accumulate the older blocks, warps 0..CW-1 share the
+// critical block jb-1 and the diagonal product with D_jb.
+__global__ void __launch_bounds__(TW * 32) k_trsv_lower_df(int N, const float4* __restrict__ L,
+                                                          const float4* __restrict__ D,
+                                                          const double2* __restrict__ y,
+                                                          float4* __restrict__ z, unsigned* flags,
+                                                          unsigned* ticket, unsigned epoch,
+                                                          int* status) {
+  __shared__ cacc part[TW][NB];
+  __shared__ cdf Ds[NB][NB + 1];
+  __shared__ cdf vsh[NB];
+  __shared__ int s_jb;
+  if (threadIdx.x == 0) s_jb = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int jb = s_jb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = jb * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Ds[r][c] = (r0 + r < N) ? ld4(D[((size_t)jb * NB + r) * NB + c]) : czero();
+  }
+  const bool row_ok = r0 + lane < N;
+  const float4* Lrow = L + (size_t)(row_ok ? r0 + lane : 0) * N;
+  cacc acc = cacc_zero();
+  for (int m = warp - CW; warp >= CW && m < jb - 1; m += TW - CW) {
+    if (lane == 0) wait_flag(flags + m, epoch, status);
+    __syncwarp();
+    const cdf zm = ldcg4(z + m * NB + lane);
+#pragma unroll 8
+    for (int c = 0; c < NB; ++c) cacc_mul(acc, ld4(__ldg(Lrow + m * NB + c)), shfl_cdf(zm, c));
+  }
+  if (warp >= CW) part[warp][lane] = acc;
+  const int mc = jb - 1;
+  cdf lv[CPW];
+#pragma unroll
+  for (int q = 0; q < CPW; ++q)
+    lv[q] = (warp < CW && mc >= 0) ? ld4(__ldg(Lrow + mc * NB + warp * CPW + q)) : czero();
+  // the right-hand side, converted off the chain
+  const double2 yv = (warp == 0 && row_ok) ? y[r0 + lane] : make_double2(0.0, 0.0);
+  const cdf yc = cdf_make(df_from(yv.x), df_from(yv.y));
+  __syncthreads();
+  if (warp >= CW) return;
+  cacc p = cacc_zero();
+  if (mc >= 0) {
+    if (lane == 0) wait_flag(flags + mc, epoch, status);
+    __syncwarp();
+    const cdf zm = ldcg4(z + mc * NB + lane);
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) cacc_mul(p, lv[q], shfl_cdf(zm, warp * CPW + q));
+  }
+  part[warp][lane] = p;
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    cacc s = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < TW; ++w) s = cacc_merge(s, part[w][lane]);
+    vsh[lane] = row_ok ? cdf_sub(yc, cacc_val(s)) : czero();
+  }
+  named_sync(1, CW * 32);
+  cacc o = cacc_zero();
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp * CPW + q;
+    cacc_mul(o, Ds[lane][c], vsh[c]);
+  }
+  part[warp][lane] = o;
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    cacc s = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < CW; ++w) s = cacc_merge(s, part[w][lane]);
+    if (row_ok) z[r0 + lane] = st4(cacc_val(s));
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) st_release(flags + jb, epoch);
+  }
+}
+
+// Backward solve L^H w = z (double-floats), out = w or -i w in FP64.
+__global__ void __launch_bounds__(TW * 32) k_trsv_upper_df(int N, const float4* __restrict__ L,
+                                                          const float4* __restrict__ D,
+                                                          const float4* __restrict__ z,
+                                                          double2* __restrict__ w_out, bool minus_i,
+                                                          float4* __restrict__ wbuf, unsigned* flags,
+                                                          unsigned* ticket, unsigned epoch,
+                                                          int* status) {
+  __shared__ cacc part[TW][NB];
+  __shared__ cdf Ds[NB][NB + 1];
+  __shared__ cdf vsh[NB];
+  __shared__ int s_jb;
+  const int nblk = (N + NB - 1) / NB;
+  if (threadIdx.x == 0) s_jb = nblk - 1 - (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int jb = s_jb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = jb * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Ds[r][c] = (r0 + r < N) ? ld4(D[((size_t)jb * NB + r) * NB + c]) : czero();
+  }
+  const bool col_ok = r0 + lane < N;
+  cacc acc = cacc_zero();
+  for (int m = nblk - 1 - (warp - CW); warp >= CW && m >= jb + 2; m -= TW - CW) {
+    if (lane == 0) wait_flag(flags + m, epoch, status);
+    __syncwarp();
+    const cdf wm = (m * NB + lane < N) ? ldcg4(wbuf + m * NB + lane) : czero();
+#pragma unroll 8
+    for (int c = 0; c < NB; ++c) {
+      const cdf l = (m * NB + c < N && col_ok) ? ld4(__ldg(L + (size_t)(m * NB + c) * N + r0 + lane))
+                                                 : czero();
+      cacc_cmul(acc, l, shfl_cdf(wm, c));
+    }
+  }
+  if (warp >= CW) part[warp][lane] = acc;
+  const int mc = jb + 1;
+  cdf lv[CPW];
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp * CPW + q;
+    lv[q] = (warp < CW && mc < nblk && mc * NB + c < N && col_ok)
+                ? ld4(__ldg(L + (size_t)(mc * NB + c) * N + r0 + lane))
+                : czero();
+  }
+  const cdf zc = (warp == 0 && col_ok) ? ld4(z[r0 + lane]) : czero();
+  __syncthreads();
+  if (warp >= CW) return;
+  cacc p = cacc_zero();
+  if (mc < nblk) {
+    if (lane == 0) wait_flag(flags + mc, epoch, status);
+    __syncwarp();
+    const cdf wm = (mc * NB + lane < N) ? ldcg4(wbuf + mc * NB + lane) : czero();
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) cacc_cmul(p, lv[q], shfl_cdf(wm, warp * CPW + q));
+  }
+  part[warp][lane] = p;
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    cacc s = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < TW; ++w) s = cacc_merge(s, part[w][lane]);
+    vsh[lane] = col_ok ? cdf_sub(zc, cacc_val(s)) : czero();
+  }
+  named_sync(1, CW * 32);
+  // w_r = sum_c conj(D_cr) v_c
+  cacc o = cacc_zero();
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp * CPW + q;
+    cacc_cmul(o, Ds[c][lane], vsh[c]);
+  }
+  part[warp][lane] = o;
+  named_sync(1, CW * 32);
+  if (warp == 0) {
+    cacc s = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < CW; ++w) s = cacc_merge(s, part[w][lane]);
+    const cdf wv = cacc_val(s);
+    if (col_ok) wbuf[r0 + lane] = st4(wv);
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) st_release(flags + jb, epoch);
+    if (col_ok) {
+      const double re = df_to(wv.re), im = df_to(wv.im);
+      w_out[r0 + lane] = minus_i ? make_double2(im, -re) : make_double2(re, im);
+    }
+  }
+}
+
+}  // namespace dfs
+
+// ---------------------------------------------------------------------------- launchers
+
+void launch_shift_mix_df(int N, const double2* S0, const double2* S1, double eps, double theta,
+                         void* A, cudaStream_t s) {
+  const size_t NN = (size_t)N * N;
+  size_t g = (NN + 255) / 256;
+  if (g > 4096) g = 4096;
+  dfs::k_shift_mix_df<<<(unsigned)g, 256, 0, s>>>(N, S0, S1, eps, theta, (float4*)A);
+}
+
+int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, int nbatch,
+                       int* status, cudaStream_t s) {
+  using namespace dfs;
+  Batch mb;
+  for (int q = 0; q < 2; ++q) {
+    const int k = (nbatch > 1 && q == 1) ? 1 : 0;
+    mb.m[q] = (float4*)A[k];
+    mb.inv[q] = (float2*)inv[k];
+    mb.D[q] = (float4*)D[k];
+  }
+  const int T = (N + NB - 1) / NB;
+  int launches = 0;
+  for (int jb = 0; jb < T; ++jb) {
+    k_potrf_df<<<dim3(1, nbatch), PF_THREADS, 0, s>>>(N, mb, jb, status);
+    ++launches;
+    const int rest = T - jb - 1;
+    if (rest > 0) {
+      const int rows = N - (jb + 1) * NB;
+      k_trsm_df<<<dim3((rows + TR_WARPS - 1) / TR_WARPS, nbatch), TR_WARPS * 32, 0, s>>>(N, mb, jb);
+      k_herk_df<<<dim3(rest * (rest + 1) / 2, nbatch), 256, 0, s>>>(N, mb, jb);
+      launches += 2;
+    }
+  }
+  k_trtri_df<<<dim3(T, nbatch), 128, 0, s>>>(N, mb);
+  return launches + 1;
+}
+
+void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y, void* work,
+                          double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
+                          unsigned epoch, int* status, cudaStream_t s) {
+  using namespace dfs;
+  const int nblk = (N + NB - 1) / NB;
+  cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
+  float4* zb = (float4*)work;
+  k_trsv_lower_df<<<nblk, TW * 32, 0, s>>>(N, (const float4*)L, (const float4*)D, y, zb, flags,
+                                            tickets, epoch, status);
+  k_trsv_upper_df<<<nblk, TW * 32, 0, s>>>(N, (const float4*)L, (const float4*)D, zb, out, minus_i,
+                                            zb + N, flags + nblk, tickets + 1, epoch, status);
+}
+
+}  // namespace icwf

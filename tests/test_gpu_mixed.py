@@ -94,3 +94,27 @@ def test_mixed_observables_vs_fp64_oracle(mode):
     assert l1x < 1e-3 and l1R < 1e-3 and l1p < 1e-3, (l1x, l1R, l1p)
     assert abs(ob["norm"] - oo["norm"]) < 1e-3
     sim.close()
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("N", [40, 300])
+def test_double_float_solve_residual(mode, N):
+    """The mixed modes factorise S + eps I and solve in double-float arithmetic (~48 bits): the
+    initial coefficients satisfy (S + eps I) C = b far beyond FP32 accuracy, with S as stored (FP64)
+    and b = <psi_a chi_a | Psi0> recomputed here from the library's own CWFs."""
+    # BF16x3 leaves ~3e-6 relative noise in S: above N ~ 300 it needs a larger regulariser
+    eps = 1e-3 if (mode == "bf16x3" and N >= 300) else EPS_MIXED
+    w = shin_metiu(n_traj=N, svd_rel_cutoff=1e-8, s_reg_eps=eps)
+    sim = g.Icwf(g.params_from(w, precision=MODES[mode]), w.V)
+    sim.init_from_density(w.psi0, 0)
+    st = sim.state()
+    S = sim.matrices()["S"]
+    # the library computes b from its FP64 slices before storing the CWFs as complex64; slice
+    # the same way here (oracle init with the library's positions) to get those FP64 slices
+    o = oracle_for(w)
+    ost = o.init_from_positions(w.psi0, st["x"], st["R"])
+    b = w.dx * w.dR * np.einsum("ia,ja,ij->a", ost.psi.conj(), ost.chi.conj(), w.psi0)
+    r = (S + eps * np.eye(N)) @ st["C"] - b
+    # a single-precision solve would leave ~1e-3 here; the 48-bit one stays near 1e-12
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-9
+    sim.close()
