@@ -41,7 +41,7 @@ constexpr int A_TILE = BM * ROWB;     // 16 KB
 constexpr int B_TILE = BNT * ROWB;    // 4 KB
 // stage layout: A_P_hi, A_P_lo, A_Q_hi, A_Q_lo, B_P_hi, B_P_lo, B_Q_hi, B_Q_lo
 constexpr int STAGE_BYTES = 4 * A_TILE + 4 * B_TILE;   // 80 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ket factors*/;
 constexpr int TMEM_COLS = 512;
 // TMEM column map: per side s (0 = x, 1 = R) accumulators PP, PQ, QP, QQ at 32 columns each
 constexpr int COL_ACC = 0;       // [0, 256): g accumulators, side-major
@@ -205,6 +205,8 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
   uint64_t* drain = acc_empty + 1;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  float* ket_ux = (float*)(tmem_slot + 4);     // 32 floats
+  float* ket_wR = ket_ux + BNT;                // 32 floats
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int I, J, q;
@@ -330,11 +332,30 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
     const float dx = args.dx, dR = args.dR;
     for (int g = 0; g < G; ++g) {
       const bool ok = mbar_wait(acc_full, (unsigned)g & 1u, abort_flag, args.status);
-      if (!__all_sync(0xffffffffu, ok)) break;
+      // one decision for all four epilogue warps (they meet at named barriers below)
+      uint32_t all_ok;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+          "bar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+          : "=r"(all_ok)
+          : "r"((uint32_t)ok)
+          : "memory");
+      if (!all_ok) break;
       fence_after();
       const float sg = g ? (float)args.sig[g - 1] : 0.f;
       const float uxa = (g && a_ok) ? (float)args.px[(size_t)(g - 1) * N + a] : 0.f;
       const float wRa = (g && a_ok) ? (float)args.pR[(size_t)(g - 1) * N + a] : 0.f;
+      if (g) {
+        // the kets' factor values for this Gram, staged once in shared memory
+        if (row < BNT) {
+          const int b = b0 + row;
+          ket_ux[row] = b < N ? (float)args.px[(size_t)(g - 1) * N + b] : 0.f;
+        } else if (row < 2 * BNT) {
+          const int b = b0 + row - BNT;
+          ket_wR[row - BNT] = b < N ? (float)args.pR[(size_t)(g - 1) * N + b] : 0.f;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
 #pragma unroll 1
       for (int c8 = 0; c8 < BNT; c8 += 8) {
         float xpp[8], xpq[8], xqp[8], xqq[8], rpp[8], rpq[8], rqp[8], rqq[8];
@@ -383,10 +404,8 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
           tmem_wait_ld();
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const int b = b0 + c8 + e;
-            const bool b_ok = b < N;
-            const float uxb = b_ok ? (float)args.px[(size_t)(g - 1) * N + b] : 0.f;
-            const float wRb = b_ok ? (float)args.pR[(size_t)(g - 1) * N + b] : 0.f;
+            const float uxb = ket_ux[c8 + e];
+            const float wRb = ket_wR[c8 + e];
             // (A - u(x_b) S1) (B - w(R_b) S2)
             const float atr = Ar[e] - uxb * s1r[e], ati = Ai[e] - uxb * s1i[e];
             const float btr = Br[e] - wRb * s2r[e], bti = Bi[e] - wRb * s2i[e];
@@ -409,6 +428,7 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
       }
       fence_before();
       mbar_arrive(acc_empty);
+      asm volatile("bar.sync 1, 128;" ::: "memory");   // ket_ux / ket_wR reused by the next Gram
     }
     // final: S = S1 o S2; Heff(a, b) = H - d_b S; Heff(b, a) = HT - d_a conj(S)
     const int aborted = __shfl_sync(0xffffffffu, *abort_flag, 0);

@@ -125,7 +125,7 @@ constexpr int PF_THREADS = 256;
 __global__ void __launch_bounds__(PF_THREADS) k_potrf_df(int N, Batch mb, int jb, int* status) {
   __shared__ cdf L[NB][NB + 1];
   __shared__ df yv[NB];
-  __shared__ df y2s;
+  __shared__ df y2b[2];   // y^2 of the current column, double-buffered by column parity
   float4* A = mb.m[blockIdx.y];
   float2* inv = mb.inv[blockIdx.y];
   const int r0 = jb * NB;
@@ -137,25 +137,38 @@ __global__ void __launch_bounds__(PF_THREADS) k_potrf_df(int N, Batch mb, int jb
     L[r][c] = v;
   }
   __syncthreads();
+  // pivot 0; afterwards thread 0 updates the next pivot first (pair e = 0 is (c+1, c+1)) and
+  // computes its reciprocal square root while the other threads finish the rank-1 update, so
+  // each column needs a single barrier
+  if (threadIdx.x == 0) {
+    df d = L[0][0].re;
+    if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
+    const df y = df_rsqrt(d);
+    L[0][0] = cdf_make(df_mul(d, y), zero);
+    yv[0] = y;
+    y2b[0] = df_mul(y, y);
+  }
+  __syncthreads();
   for (int c = 0; c < NB; ++c) {
-    if (threadIdx.x == 0) {
-      df d = L[c][c].re;
-      if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
-      const df y = df_rsqrt(d);
-      L[c][c] = cdf_make(df_mul(d, y), zero);
-      yv[c] = y;
-      y2s = df_mul(y, y);
-    }
-    __syncthreads();
     if (c > 0) {
+      // column c-1 is no longer read: scale it now
       const int r = c + (int)threadIdx.x;
       if (r < NB) L[r][c - 1] = cdf_scale(L[r][c - 1], yv[c - 1]);
     }
-    const df y2 = y2s;
-    const int m = NB - 1 - c;
-    for (int e = threadIdx.x; e < m * m; e += PF_THREADS) {
-      const int r = c + 1 + e / m, q = c + 1 + e % m;
-      if (q <= r) L[r][q] = cdf_sub(L[r][q], cdf_scale(cdf_mul_conj(L[r][c], L[q][c]), y2));
+    const df y2 = y2b[c & 1];
+    // lower-triangle pairs c < q <= r: thread t takes row c + 1 + t/8 and every 8th column
+    const int r = c + 1 + (int)(threadIdx.x >> 3);
+    for (int q = c + 1 + (int)(threadIdx.x & 7); r < NB && q <= r; q += 8) {
+      L[r][q] = cdf_sub(L[r][q], cdf_scale(cdf_mul_conj(L[r][c], L[q][c]), y2));
+      if (threadIdx.x == 0) {
+        // thread 0 just produced the pivot of column c + 1
+        df d = L[c + 1][c + 1].re;
+        if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
+        const df y = df_rsqrt(d);
+        L[c + 1][c + 1] = cdf_make(df_mul(d, y), zero);
+        yv[c + 1] = y;
+        y2b[(c + 1) & 1] = df_mul(y, y);
+      }
     }
     __syncthreads();
   }
