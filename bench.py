@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="tf32x3", choices=list(MODES))
     ap.add_argument("--n-traj", type=int, default=1024)
+    ap.add_argument("--nx", type=int, default=1024, help="electron grid points (profiling cases)")
+    ap.add_argument("--nR", type=int, default=512, help="nuclear grid points (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -49,9 +51,9 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(n_traj, cutoff, eps):
+def make_workload(n_traj, cutoff, eps, nx=1024, nR=512):
     from workloads import WORKLOADS
-    return WORKLOADS["sm_paper"](n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps)
+    return WORKLOADS["sm_paper"](n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps, nx=nx, nR=nR)
 
 
 def workload_name(w):
@@ -200,7 +202,7 @@ def run_ours(args, rank, ws, local):
 
     torch.cuda.set_device(local)
     prec, dtype_name, cutoff, eps = MODES[args.mode]
-    w = make_workload(args.n_traj, cutoff, eps)
+    w = make_workload(args.n_traj, cutoff, eps, args.nx, args.nR)
     params = g.params_from(w, precision=prec)
 
     sim = g.Icwf(params, w.V)
@@ -452,7 +454,7 @@ def run_reference(args, rank, ws):
     if rank != 0:
         return None
     prec, dtype_name, cutoff, eps = MODES[args.mode]
-    w = make_workload(args.n_traj, cutoff, eps)
+    w = make_workload(args.n_traj, cutoff, eps, args.nx, args.nR)
     from oracle.icwf import Icwf as Oracle, Params
     p = Params(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, w.dt,
                w.n_traj, w.svd_rel_cutoff, w.s_reg_eps)

@@ -76,6 +76,7 @@ struct icwf_ctx {
   double2* C = nullptr;
   double2* kk[4] = {nullptr, nullptr, nullptr, nullptr};
   double2 *y = nullptr, *work = nullptr;
+  float* cf32 = nullptr;   // C in FP32 (mixed modes)
   double2 *S[2] = {nullptr, nullptr}, *H[2] = {nullptr, nullptr};
   double2 *L[2] = {nullptr, nullptr}, *Lh = nullptr;
   double *invL[2] = {nullptr, nullptr}, *invLh = nullptr;   // reciprocal Cholesky pivots
@@ -137,6 +138,7 @@ JobView view(icwf_ctx* h) {
   j.px = h->px; j.pR = h->pR; j.d = h->dvec;
   j.kinx = h->kinx; j.kinR = h->kinR; j.twx = h->twx; j.twR = h->twR;
   j.status = h->status;
+  j.scratch_f32 = h->mixed ? h->cf32 : nullptr;
   return j;
 }
 
@@ -322,7 +324,7 @@ void step_once(icwf_ctx* h) {
     ProfScope ps(h, F_VELOCITY);
     if (h->mixed) launch_velocity<float>(j, h->C, h->stream);
     else launch_velocity<double>(j, h->C, h->stream);
-    h->launches += 1;
+    h->launches += h->mixed ? 2 : 1;
   }
   {
     ProfScope ps(h, F_PROPAGATE);
@@ -547,6 +549,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
       (size_t)N * nx * cw, (size_t)N * nR * cw,
       (size_t)N * 8 * 4, (size_t)K * N * 8 * 2, (size_t)N * 8,
       (size_t)N * 16 * 8,  // C, k1..k4, y, work(2N)
+      (size_t)N * 8,       // C in FP32
       NN * 16 * 7,         // S[2], H[2], L[2], Lh
       (size_t)N * 8, (size_t)N * 8, (size_t)N * 8,   // reciprocal pivots of L[2], Lh
       (size_t)N * 512, (size_t)N * 512, (size_t)N * 512,   // inverted diagonal blocks
@@ -590,6 +593,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   for (int q = 0; q < 4; ++q) h->kk[q] = (double2*)a.take((size_t)N * 16);
   h->y = (double2*)a.take((size_t)N * 16);
   h->work = (double2*)a.take((size_t)2 * N * 16);
+  h->cf32 = (float*)a.take((size_t)N * 8);
   for (int q = 0; q < 2; ++q) {
     h->S[q] = (double2*)a.take(NN * 16);
     h->H[q] = (double2*)a.take(NN * 16);

@@ -49,6 +49,7 @@ struct JobView {
   const void* twx;        // nx/2 twiddles exp(-2 pi i k / nx)
   const void* twR;
   int* status;
+  float* scratch_f32;     // 2N floats (mixed modes: C in FP32 for the velocity kernel), or NULL
 };
 
 // Per-kernel-family timing hook (api.cpp implements it).

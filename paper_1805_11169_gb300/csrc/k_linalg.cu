@@ -298,18 +298,21 @@ __global__ void __launch_bounds__(256) k_matvec(int N, const double2* __restrict
   const int a = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (a >= N) return;
-  double2 acc = make_double2(0, 0);
+  // four independent partial sums: dependent FP64 operations are long-latency on this GPU
+  double2 t[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
   const double2* h0 = H0 + (size_t)a * N;
   const double2* h1 = H1 + (size_t)a * N;
-  for (int b = lane; b < N; b += 32) {
+  int q = 0;
+  for (int b = lane; b < N; b += 32, q = (q + 1) & 3) {
     double2 v = C[b];
     if (kp) { const double2 k = kp[b]; v.x += c * k.x; v.y += c * k.y; }
     double2 h;
     if (theta == 0.0) h = h0[b];
     else if (theta == 1.0) h = h1[b];
     else h = make_double2(0.5 * (h0[b].x + h1[b].x), 0.5 * (h0[b].y + h1[b].y));
-    cfma(acc, h, v);
+    cfma(t[q], h, v);
   }
+  double2 acc = cadd(cadd(t[0], t[1]), cadd(t[2], t[3]));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);

@@ -98,6 +98,120 @@ __global__ void __launch_bounds__(256) k_velocity(JobView j, const double2* __re
   }
 }
 
+// FP32 version for the mixed modes (complex64 CWFs): stencil weights, interpolation and the
+// three sums in FP32 (FP64 arithmetic is slow and long-latency on this GPU); the position update
+// itself stays FP64.  Pinned factor values at the new positions in FP32 as well (the tensor-core
+// assembly consumes them in FP32).
+struct StencilF {
+  int i0;
+  float w[4];
+  float dw[4];
+};
+__device__ __forceinline__ StencilF lagrange4f(double p, double lo, double d, int n) {
+  StencilF st;
+  const float s = (float)((p - lo) / d) - 0.5f;
+  int i0 = (int)floorf(s) - 1;
+  i0 = i0 < 0 ? 0 : (i0 > n - 4 ? n - 4 : i0);
+  const float u = s - (float)i0;
+  const float u1 = u - 1.f, u2 = u - 2.f, u3 = u - 3.f;
+  const float inv = (float)(1.0 / d);
+  st.i0 = i0;
+  st.w[0] = -(u1 * u2 * u3) * (1.f / 6.f);
+  st.w[1] = (u * u2 * u3) * 0.5f;
+  st.w[2] = -(u * u1 * u3) * 0.5f;
+  st.w[3] = (u * u1 * u2) * (1.f / 6.f);
+  st.dw[0] = -((u2 * u3) + (u1 * u3) + (u1 * u2)) * (1.f / 6.f) * inv;
+  st.dw[1] = ((u2 * u3) + (u * u3) + (u * u2)) * 0.5f * inv;
+  st.dw[2] = -((u1 * u3) + (u * u3) + (u * u1)) * 0.5f * inv;
+  st.dw[3] = ((u1 * u2) + (u * u2) + (u * u1)) * (1.f / 6.f) * inv;
+  return st;
+}
+
+__global__ void __launch_bounds__(256) k_velocity_f32(JobView j, const double2* __restrict__ C,
+                                                      double xlo, double xhi, double Rlo, double Rhi,
+                                                      float inv_mx, float inv_mR, float* __restrict__ Cf) {
+  const int a = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (a >= j.N) return;
+  const double xa = j.x[a], Ra = j.R[a];
+  const StencilF sx = lagrange4f(xa, j.x_min, j.dx, j.nx);
+  const StencilF sR = lagrange4f(Ra, j.R_min, j.dR, j.nR);
+  const float2* psi = (const float2*)j.psi;
+  const float2* chi = (const float2*)j.chi;
+  float2 den = make_float2(0.f, 0.f), nux = den, nuR = den;
+  for (int b = lane; b < j.N; b += 32) {
+    const float2* pc = psi + (size_t)b * j.nx + sx.i0;
+    const float2* qc = chi + (size_t)b * j.nR + sR.i0;
+    float2 E1 = make_float2(0.f, 0.f), G1 = E1, E2 = E1, G2 = E1;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float2 p = pc[m], q = qc[m];
+      E1.x = fmaf(sx.w[m], p.x, E1.x);  E1.y = fmaf(sx.w[m], p.y, E1.y);
+      G1.x = fmaf(sx.dw[m], p.x, G1.x); G1.y = fmaf(sx.dw[m], p.y, G1.y);
+      E2.x = fmaf(sR.w[m], q.x, E2.x);  E2.y = fmaf(sR.w[m], q.y, E2.y);
+      G2.x = fmaf(sR.dw[m], q.x, G2.x); G2.y = fmaf(sR.dw[m], q.y, G2.y);
+    }
+    const float2 cb = make_float2(Cf[2 * b], Cf[2 * b + 1]);
+    const float2 c1 = cmul(cb, E1);
+    den = cadd(den, cmul(c1, E2));
+    nux = cadd(nux, cmul(cmul(cb, G1), E2));
+    nuR = cadd(nuR, cmul(c1, G2));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    den.x += __shfl_xor_sync(0xffffffffu, den.x, off);
+    den.y += __shfl_xor_sync(0xffffffffu, den.y, off);
+    nux.x += __shfl_xor_sync(0xffffffffu, nux.x, off);
+    nux.y += __shfl_xor_sync(0xffffffffu, nux.y, off);
+    nuR.x += __shfl_xor_sync(0xffffffffu, nuR.x, off);
+    nuR.y += __shfl_xor_sync(0xffffffffu, nuR.y, off);
+  }
+  const float dd = den.x * den.x + den.y * den.y;
+  const float vx = (nux.y * den.x - nux.x * den.y) / dd * inv_mx;
+  const float vR = (nuR.y * den.x - nuR.x * den.y) / dd * inv_mR;
+  double xn = xa + j.dt * (double)vx;
+  double Rn = Ra + j.dt * (double)vR;
+  if (lane == 0) {
+    if (!isfinite(vx) || !isfinite(vR)) set_flag(j.status, ST_NONFINITE);
+    int cl = 0;
+    if (xn < xlo) { xn = xlo; ++cl; } else if (xn > xhi) { xn = xhi; ++cl; }
+    if (Rn < Rlo) { Rn = Rlo; ++cl; } else if (Rn > Rhi) { Rn = Rhi; ++cl; }
+    if (cl) atomicAdd(j.status + STATUS_CLAMPED, cl);
+    j.xo[a] = xa; j.Ro[a] = Ra;
+    j.x[a] = xn;  j.R[a] = Rn;
+  }
+  xn = __shfl_sync(0xffffffffu, xn < xlo ? xlo : (xn > xhi ? xhi : xn), 0);
+  Rn = __shfl_sync(0xffffffffu, Rn < Rlo ? Rlo : (Rn > Rhi ? Rhi : Rn), 0);
+  if (!isfinite(xn)) xn = xa;
+  if (!isfinite(Rn)) Rn = Ra;
+  const StencilF tx = lagrange4f(xn, j.x_min, j.dx, j.nx);
+  const StencilF tR = lagrange4f(Rn, j.R_min, j.dR, j.nR);
+  float part = 0.f;
+  for (int k = lane; k < j.K; k += 32) {
+    const double* u = j.U + (size_t)k * j.nx + tx.i0;
+    const double* w = j.W + (size_t)k * j.nR + tR.i0;
+    const float uk = tx.w[0] * (float)u[0] + tx.w[1] * (float)u[1] + tx.w[2] * (float)u[2] + tx.w[3] * (float)u[3];
+    const float wk = tR.w[0] * (float)w[0] + tR.w[1] * (float)w[1] + tR.w[2] * (float)w[2] + tR.w[3] * (float)w[3];
+    j.px[(size_t)k * j.N + a] = uk;
+    j.pR[(size_t)k * j.N + a] = wk;
+    part += (float)j.sig[k] * (uk * wk);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  if (lane == 0) {
+    const double* v1 = j.v1 + tx.i0;
+    const double* v2 = j.v2 + tR.i0;
+    const float a1 = tx.w[0] * (float)v1[0] + tx.w[1] * (float)v1[1] + tx.w[2] * (float)v1[2] + tx.w[3] * (float)v1[3];
+    const float a2 = tR.w[0] * (float)v2[0] + tR.w[1] * (float)v2[1] + tR.w[2] * (float)v2[2] + tR.w[3] * (float)v2[3];
+    j.d[a] = (double)(a1 + a2 + part);
+  }
+}
+
+__global__ void k_coeff_to_f32(int N, const double2* __restrict__ C, float* __restrict__ Cf) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < N) { Cf[2 * b] = (float)C[b].x; Cf[2 * b + 1] = (float)C[b].y; }
+}
+
 // Pinned factor values at the current positions without moving them (initialisation).
 __global__ void k_pinned_only(JobView j) {
   const int a = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -134,6 +248,12 @@ void launch_velocity(const JobView& j, const double2* C, cudaStream_t s) {
   const double Rlo = j.R_min + 0.5 * j.dR, Rhi = j.R_min + (j.nR - 0.5) * j.dR;
   if (C == nullptr) {
     k_pinned_only<<<grid, warps * 32, 0, s>>>(j);
+    return;
+  }
+  if (sizeof(T) == 4 && j.scratch_f32) {
+    k_coeff_to_f32<<<(j.N + 255) / 256, 256, 0, s>>>(j.N, C, j.scratch_f32);
+    k_velocity_f32<<<grid, warps * 32, 0, s>>>(j, C, xlo, xhi, Rlo, Rhi, (float)j.inv_mx,
+                                               (float)j.inv_mR, j.scratch_f32);
     return;
   }
   k_velocity<T><<<grid, warps * 32, 0, s>>>(j, C, xlo, xhi, Rlo, Rhi);
