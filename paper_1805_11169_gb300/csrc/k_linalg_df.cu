@@ -511,6 +511,306 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_upper_df(int N, const float4* 
   }
 }
 
+// ---------------------------------------------------------------------------- cluster solve
+
+// Both triangular solves of one RK4 stage in a single launch of one 8-CTA thread-block cluster.
+// Every CTA keeps the whole forward solution z and backward solution w in its shared memory.
+// CTA rank r owns block rows jb = r, r + 8, ...; when it finishes a block it pushes the 32 values
+// to all eight CTAs with bulk shared-to-shared copies (DSMEM) that complete the transaction count
+// of the receiver's per-block mbarrier, so consumers wait on a local barrier instead of polling
+// global memory.  The loops are block-major: on the arrival of block m every CTA adds that block's
+// products to all of its pending rows, and finishes its own row m + 1 (forward) / m - 1 (backward)
+// as soon as the block it depends on is in.  Products use compensated double-float dot products;
+// the critical block's columns are split over the eight warps and merged through shared memory.
+constexpr int CL = 8;          // CTAs per cluster
+constexpr int CRPC = 8;        // maximum block rows per CTA (N <= CL * CRPC * 32 = 2048)
+constexpr int CTH = 256;       // threads per CTA
+constexpr unsigned long long CWAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtime_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init_c(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_c(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_c(uint64_t* b, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(s_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase 0 of a local block barrier
+__device__ __forceinline__ bool block_wait(uint64_t* b, volatile int* abort_flag, int* status) {
+  const unsigned long long t0 = gtime_ns();
+  while (!mbar_test_c(b, 0u)) {
+    if (*abort_flag) return false;
+    if (gtime_ns() - t0 > CWAIT_NS) {
+      *abort_flag = 1;
+      set_flag(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+// push 512 bytes of a finished block from local staging to every CTA of the cluster
+__device__ __forceinline__ void push_block(const float4* stage, float4* dst_local, uint64_t* bar_local) {
+  const uint32_t src = s_u32(stage);
+#pragma unroll
+  for (uint32_t r = 0; r < CL; ++r) {
+    const uint32_t dst = map_rank(s_u32(dst_local), r);
+    const uint32_t bar = map_rank(s_u32(bar_local), r);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "r"(src), "r"(512u), "r"(bar)
+        : "memory");
+  }
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Shared-memory layout of the cluster solve (per CTA).
+struct CLayout {
+  float4* zs;        // nblk*32 forward solution
+  float4* ws;        // nblk*32 backward solution
+  float4* yown;      // CRPC*32 right-hand side of the own rows (double-floats)
+  float4* stage;     // 32 outgoing block
+  cacc* part;        // 8*32 cross-warp partial sums
+  cdf* vsh;          // 32
+  uint64_t* barF;    // nblk
+  uint64_t* barB;    // nblk
+  int* abort_flag;
+};
+__host__ __device__ inline size_t clayout_bytes(int nblk) {
+  return (size_t)(2 * nblk + CRPC + 1) * NB * 16 + (size_t)8 * NB * 16 + NB * 16 + (size_t)2 * nblk * 8 + 16;
+}
+__device__ __forceinline__ CLayout clayout(unsigned char* base, int nblk) {
+  CLayout c;
+  c.zs = (float4*)base;
+  c.ws = c.zs + nblk * NB;
+  c.yown = c.ws + nblk * NB;
+  c.stage = c.yown + CRPC * NB;
+  c.part = (cacc*)(c.stage + NB);
+  c.vsh = (cdf*)(c.part + 8 * NB);
+  c.barF = (uint64_t*)(c.vsh + NB);
+  c.barB = c.barF + nblk;
+  c.abort_flag = (int*)(c.barB + nblk);
+  return c;
+}
+
+// Finish block row m.  `mine` holds this warp's share of the products with all other blocks; the
+// eight shares are merged, subtracted from the right-hand side, multiplied by the inverted diagonal
+// block (D_m forward, D_m^H backward; `dk` are this warp's four columns of it, prefetched), and the
+// 32 values are pushed to every CTA of the cluster.  Backward blocks are also written to `out`.
+template <bool FWD>
+__device__ __forceinline__ void finish_block(const CLayout& c, int N, int m, const cacc& mine,
+                                             const cdf (&dk)[4], double2* out, bool minus_i) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c0w = warp * 4;
+  const int row = m * NB + lane;
+  c.part[warp * NB + lane] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    cacc s = c.part[lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) s = cacc_merge(s, c.part[w * NB + lane]);
+    const cdf rhs = FWD ? ld4(c.yown[(m / CL) * NB + lane]) : ld4(c.zs[row < N ? row : 0]);
+    c.vsh[lane] = row < N ? cdf_sub(rhs, cacc_val(s)) : czero();
+  }
+  __syncthreads();
+  cacc o = cacc_zero();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (FWD) cacc_mul(o, dk[q], c.vsh[c0w + q]);
+    else cacc_cmul(o, dk[q], c.vsh[c0w + q]);
+  }
+  c.part[warp * NB + lane] = o;
+  __syncthreads();
+  if (warp == 0) {
+    cacc s = c.part[lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) s = cacc_merge(s, c.part[w * NB + lane]);
+    const cdf v = row < N ? cacc_val(s) : czero();
+    c.stage[lane] = st4(v);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0 && !*(volatile int*)c.abort_flag)
+      push_block(c.stage, (FWD ? c.zs : c.ws) + m * NB, (FWD ? c.barF : c.barB) + m);
+    __syncwarp();
+    if (!FWD && row < N) {
+      const double re = df_to(v.re), im = df_to(v.im);
+      out[row] = minus_i ? make_double2(im, -re) : make_double2(re, im);
+    }
+  }
+  __syncthreads();
+}
+
+// Waits for block m on a local barrier; the outcome is made uniform over the CTA.
+__device__ __forceinline__ bool cta_wait_block(const CLayout& c, uint64_t* bar, int* status) {
+  const bool ok = block_wait(bar, (volatile int*)c.abort_flag, status);
+  return !__syncthreads_or(!ok);
+}
+
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(CTH, 1)
+k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restrict__ D,
+                     const double2* __restrict__ y, double2* __restrict__ out, bool minus_i,
+                     int* status) {
+  extern __shared__ __align__(128) unsigned char csm[];
+  const int nblk = (N + NB - 1) / NB;
+  const CLayout c = clayout(csm, nblk);
+  const int rank = (int)cluster_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0w = warp * 4;                        // this warp's 4 columns of a block
+
+  if (threadIdx.x == 0) {
+    for (int m = 0; m < nblk; ++m) {
+      mbar_init_c(c.barF + m, 1);
+      mbar_init_c(c.barB + m, 1);
+    }
+    *c.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int m = 0; m < nblk; ++m) {
+      mbar_expect_c(c.barF + m, 512u);
+      mbar_expect_c(c.barB + m, 512u);
+    }
+  }
+  // right-hand side of the own rows, converted to double-floats once
+  for (int e = threadIdx.x; e < CRPC * NB; e += CTH) {
+    const int row = (rank + CL * (e / NB)) * NB + e % NB;
+    const double2 yv = row < N ? y[row] : make_double2(0.0, 0.0);
+    c.yown[e] = st4(cdf_make(df_from(yv.x), df_from(yv.y)));
+  }
+  __syncthreads();
+  cluster_sync();
+
+  cacc acc[CRPC];
+  cdf dk[4], lk[4];
+  // ------------------------------------------------ forward: L z = y
+#pragma unroll
+  for (int i = 0; i < CRPC; ++i) acc[i] = cacc_zero();
+  bool alive = true;
+  if (rank == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dk[q] = lane < N ? ld4(D[(size_t)lane * NB + c0w + q]) : czero();
+    finish_block<true>(c, N, 0, cacc_zero(), dk, out, minus_i);
+  }
+  for (int m = 0; m < nblk; ++m) {
+    const int mc = m + 1;
+    const bool crit = mc < nblk && mc % CL == rank;
+    if (crit) {
+      // prefetch the critical row's operands before the wait: L[mc, m] and D_mc
+      const int row = mc * NB + lane;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        lk[q] = row < N ? ld4(__ldg(L + (size_t)row * N + m * NB + c0w + q)) : czero();
+        dk[q] = row < N ? ld4(__ldg(D + (size_t)row * NB + c0w + q)) : czero();
+      }
+    }
+    if (!cta_wait_block(c, c.barF + m, status)) { alive = false; break; }
+    cdf zc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) zc[q] = ld4(c.zs[m * NB + c0w + q]);
+    if (crit) {
+      cacc mine = cacc_zero();
+#pragma unroll
+      for (int i = 0; i < CRPC; ++i) if (rank + CL * i == mc) mine = acc[i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cacc_mul(mine, lk[q], zc[q]);
+      finish_block<true>(c, N, mc, mine, dk, out, minus_i);
+    }
+    // the remaining own rows jb > m + 1: acc += L[jb, m] z_m
+#pragma unroll
+    for (int i = 0; i < CRPC; ++i) {
+      const int jb = rank + CL * i;
+      const int row = jb * NB + lane;
+      if (jb > mc && jb < nblk && row < N) {
+        const float4* lp = L + (size_t)row * N + m * NB + c0w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cacc_mul(acc[i], ld4(__ldg(lp + q)), zc[q]);
+      }
+    }
+  }
+  // ------------------------------------------------ backward: L^H w = z
+  if (alive) {
+#pragma unroll
+    for (int i = 0; i < CRPC; ++i) acc[i] = cacc_zero();
+    const int last = nblk - 1;
+    if (last % CL == rank) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = last * NB + c0w + q;
+        dk[q] = r < N ? ld4(D[(size_t)r * NB + lane]) : czero();
+      }
+      finish_block<false>(c, N, last, cacc_zero(), dk, out, minus_i);
+    }
+    for (int m = last; m >= 0; --m) {
+      const int mc = m - 1;
+      const bool crit = mc >= 0 && mc % CL == rank;
+      if (crit) {
+        // L[m, mc]^H and D_mc^H: this warp's four rows of block m / of D_mc, column `lane`
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rm = m * NB + c0w + q;
+          lk[q] = rm < N ? ld4(__ldg(L + (size_t)rm * N + mc * NB + lane)) : czero();
+          dk[q] = ld4(__ldg(D + (size_t)(mc * NB + c0w + q) * NB + lane));
+        }
+      }
+      if (!cta_wait_block(c, c.barB + m, status)) break;
+      cdf wc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wc[q] = ld4(c.ws[m * NB + c0w + q]);
+      if (crit) {
+        cacc mine = cacc_zero();
+#pragma unroll
+        for (int i = 0; i < CRPC; ++i) if (rank + CL * i == mc) mine = acc[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cacc_cmul(mine, lk[q], wc[q]);
+        finish_block<false>(c, N, mc, mine, dk, out, minus_i);
+      }
+      // the remaining own rows jb < m - 1: acc += L[m, jb]^H w_m
+#pragma unroll
+      for (int i = 0; i < CRPC; ++i) {
+        const int jb = rank + CL * i;
+        if (jb < mc) {
+          const int col = jb * NB + lane;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int rm = m * NB + c0w + q;
+            if (rm < N) cacc_cmul(acc[i], ld4(__ldg(L + (size_t)rm * N + col)), wc[q]);
+          }
+        }
+      }
+    }
+  }
+  // no CTA leaves while copies to or from it may still be in flight
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  __syncthreads();
+  cluster_sync();
+}
+
+size_t cluster_solve_smem(int N) { return clayout_bytes((N + NB - 1) / NB); }
+
 }  // namespace dfs
 
 // ---------------------------------------------------------------------------- launchers
@@ -555,6 +855,19 @@ void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y,
                           unsigned epoch, int* status, cudaStream_t s) {
   using namespace dfs;
   const int nblk = (N + NB - 1) / NB;
+  if (nblk <= CL * CRPC) {
+    // one 8-CTA cluster, both passes in one launch
+    const size_t sm = cluster_solve_smem(N);
+    static size_t sm_set = 0;
+    if (sm > sm_set) {
+      cudaFuncSetAttribute(k_chol_solve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cluster_solve_smem(CL * CRPC * NB));
+      sm_set = cluster_solve_smem(CL * CRPC * NB);
+    }
+    k_chol_solve_cluster<<<CL, CTH, sm, s>>>(N, (const float4*)L, (const float4*)D, y, out, minus_i,
+                                             status);
+    return;
+  }
   cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
   float4* zb = (float4*)work;
   k_trsv_lower_df<<<nblk, TW * 32, 0, s>>>(N, (const float4*)L, (const float4*)D, y, zb, flags,

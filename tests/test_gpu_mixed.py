@@ -97,13 +97,15 @@ def test_mixed_observables_vs_fp64_oracle(mode):
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-@pytest.mark.parametrize("N", [40, 300])
+@pytest.mark.parametrize("N", [40, 300, 2048, 2049])
 def test_double_float_solve_residual(mode, N):
     """The mixed modes factorise S + eps I and solve in double-float arithmetic (~48 bits): the
     initial coefficients satisfy (S + eps I) C = b far beyond FP32 accuracy, with S as stored (FP64)
-    and b = <psi_a chi_a | Psi0> recomputed here from the library's own CWFs."""
+    and b = <psi_a chi_a | Psi0> recomputed here from the library's own CWFs.  N <= 2048 runs both
+    triangular solves in one thread-block cluster (2048 = its largest size); N = 2049 takes the
+    per-block kernels with a ragged last block."""
     # BF16x3 leaves ~3e-6 relative noise in S: above N ~ 300 it needs a larger regulariser
-    eps = 1e-3 if (mode == "bf16x3" and N >= 300) else EPS_MIXED
+    eps = 1e-3 if ((mode == "bf16x3" and N >= 300) or N > 1024) else EPS_MIXED
     w = shin_metiu(n_traj=N, svd_rel_cutoff=1e-8, s_reg_eps=eps)
     sim = g.Icwf(g.params_from(w, precision=MODES[mode]), w.V)
     sim.init_from_density(w.psi0, 0)
