@@ -94,6 +94,29 @@ DF_HD df df_rsqrt(df a) {
   return y;
 }
 
+// 1 / sqrt(a), a > 0, from an FP32 estimate y0 with relative error |r0| << 1: one correction
+// y = y0 (1 + r/2 + 3 r^2/8), r = 1 - a y0^2, which is the binomial series of y0 (1 - r)^(-1/2)
+// cut after the r^2 term, so the relative error is O(r^3).  r is formed from exact products
+// (1 - t is exact for t in [1/2, 2] by Sterbenz' lemma), so it carries ~46 correct bits.
+DF_HD df df_rsqrt_refine(df a, float y0) {
+  const float p = DF_MUL(y0, y0);
+  const float pe = DF_FMA(y0, y0, -p);       // y0^2 = p + pe exactly
+  const float t = DF_MUL(a.h, p);
+  const float te = DF_FMA(a.h, p, -t);       // a.h p = t + te exactly
+  // the three small terms (each ~2^-24) first, so that r is rounded once
+  const float r = DF_SUB(DF_SUB(1.0f, t), DF_FMA(a.h, pe, DF_FMA(a.l, p, te)));
+  const float corr = DF_MUL(y0, DF_MUL(r, DF_FMA(0.375f, r, 0.5f)));
+  return fast_two_sum(y0, corr);
+}
+DF_HD df df_rsqrt1(df a) { return df_rsqrt_refine(a, DF_RSQRT(a.h)); }
+
+// Addition without the second renormalisation: the error is bounded relative to |a| + |b|
+// (not |a + b|), which is all a normwise backward-stable factorisation needs.
+DF_HD df df_add_sloppy(df a, df b) {
+  const df s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, DF_ADD(s.l, DF_ADD(a.l, b.l)));
+}
+
 // complex double-float
 struct cdf {
   df re, im;

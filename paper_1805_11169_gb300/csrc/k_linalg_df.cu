@@ -98,6 +98,18 @@ struct Batch {
   float2* inv[2];   // 1/L_cc as double-floats
   float4* D[2];     // inverted diagonal blocks
 };
+// member of a two-entry parameter array without a dynamically indexed (local-memory) copy
+template <typename T>
+__device__ __forceinline__ T pick2(T const (&a)[2], unsigned i) { return i ? a[1] : a[0]; }
+
+__device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
+  cdf r;
+  r.re.h = __shfl_sync(0xffffffffu, v.re.h, src);
+  r.re.l = __shfl_sync(0xffffffffu, v.re.l, src);
+  r.im.h = __shfl_sync(0xffffffffu, v.im.h, src);
+  r.im.l = __shfl_sync(0xffffffffu, v.im.l, src);
+  return r;
+}
 
 // ---------------------------------------------------------------------------- S + eps I
 
@@ -118,106 +130,161 @@ __global__ void k_shift_mix_df(int N, const double2* __restrict__ S0, const doub
 
 // ---------------------------------------------------------------------------- diagonal factor
 
-constexpr int PF_THREADS = 256;
+constexpr int PF_THREADS = 512;                                 // 15 update warps + 1 pivot warp
+constexpr int PF_WORKERS = PF_THREADS - 32;
+constexpr int PF_PAIRS = NB * (NB - 1) / 2;                     // (r, q), 1 <= q <= r < 32
+constexpr int PF_PER = (PF_PAIRS + PF_WORKERS - 1) / PF_WORKERS;
 
-// Same algorithm as the FP64-storage diagonal factor: double-float pivot chain, rank-1 updates
-// with y^2 from the unscaled column, column scaling one column later.
-__global__ void __launch_bounds__(PF_THREADS) k_potrf_df(int N, Batch mb, int jb, int* status) {
+// z - (x conj(w)) s with sloppy double-float additions (error relative to the operands' sizes)
+__device__ __forceinline__ cdf sub_outer(cdf z, cdf x, cdf w, df s) {
+  const df re = df_add_sloppy(df_mul(x.re, w.re), df_mul(x.im, w.im));
+  const df im = df_add_sloppy(df_mul(x.im, w.re), df_neg(df_mul(x.re, w.im)));
+  return cdf_make(df_add_sloppy(z.re, df_neg(df_mul(re, s))),
+                  df_add_sloppy(z.im, df_neg(df_mul(im, s))));
+}
+
+// Factor and invert one 32 x 32 diagonal block: L_jj L_jj^H = A_jj and D_jj = L_jj^{-1}.
+// Right-looking with unscaled columns: step c subtracts a_rc conj(a_qc) / d_c from the trailing
+// block (d_c the pivot) and columns are scaled by 1/sqrt(d_c) at the end.  A dedicated warp
+// computes the next pivot during each step (it applies column c to element (c+1, c+1) itself and
+// takes the reciprocal square root), so a column costs one barrier and the pivot chain runs
+// beside the update.  The inverse is then formed by forward substitution of the 32 unit vectors,
+// two columns per warp, with compensated (Dot2) accumulation.
+__global__ void __launch_bounds__(PF_THREADS) k_potrf_inv_df(int N, Batch mb, int jb, int* status) {
   __shared__ cdf L[NB][NB + 1];
-  __shared__ df yv[NB];
-  __shared__ df y2b[2];   // y^2 of the current column, double-buffered by column parity
-  float4* A = mb.m[blockIdx.y];
-  float2* inv = mb.inv[blockIdx.y];
+  __shared__ df yv[NB];     // 1 / sqrt(d_c)
+  __shared__ df y2v[NB];    // 1 / d_c
+  float4* A = pick2(mb.m, blockIdx.y);
+  float2* inv = pick2(mb.inv, blockIdx.y);
+  float4* D = pick2(mb.D, blockIdx.y);
   const int r0 = jb * NB;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool pivot_warp = warp == PF_THREADS / 32 - 1;
   const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
-  for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
+  for (int e = tid; e < NB * NB; e += PF_THREADS) {
     const int r = e / NB, c = e % NB;
     cdf v = cdf_make(r == c ? one : zero, zero);
     if (c <= r && r0 + r < N && r0 + c < N) v = ld4(A[(size_t)(r0 + r) * N + r0 + c]);
     L[r][c] = v;
   }
-  __syncthreads();
-  // pivot 0; afterwards thread 0 updates the next pivot first (pair e = 0 is (c+1, c+1)) and
-  // computes its reciprocal square root while the other threads finish the rank-1 update, so
-  // each column needs a single barrier
-  if (threadIdx.x == 0) {
-    df d = L[0][0].re;
-    if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
-    const df y = df_rsqrt(d);
-    L[0][0] = cdf_make(df_mul(d, y), zero);
-    yv[0] = y;
-    y2b[0] = df_mul(y, y);
+  // this worker's elements (r, q), 1 <= q <= r, packed as e = r (r - 1) / 2 + q - 1
+  int er[PF_PER], eq[PF_PER];
+#pragma unroll
+  for (int i = 0; i < PF_PER; ++i) {
+    const int e = tid + i * PF_WORKERS;
+    int r = 1;
+    while (r * (r + 1) / 2 <= e) ++r;
+    er[i] = (!pivot_warp && e < PF_PAIRS) ? r : -1;
+    eq[i] = e - r * (r - 1) / 2 + 1;
   }
   __syncthreads();
-  for (int c = 0; c < NB; ++c) {
-    if (c > 0) {
-      // column c-1 is no longer read: scale it now
-      const int r = c + (int)threadIdx.x;
-      if (r < NB) L[r][c - 1] = cdf_scale(L[r][c - 1], yv[c - 1]);
+  if (pivot_warp) {
+    df d = L[0][0].re;
+    if (!(d.h > 0.f)) {
+      if (lane == 0) set_flag(status, ST_CHOL);
+      d = one;
     }
-    const df y2 = y2b[c & 1];
-    // lower-triangle pairs c < q <= r: thread t takes row c + 1 + t/8 and every 8th column
-    const int r = c + 1 + (int)(threadIdx.x >> 3);
-    for (int q = c + 1 + (int)(threadIdx.x & 7); r < NB && q <= r; q += 8) {
-      L[r][q] = cdf_sub(L[r][q], cdf_scale(cdf_mul_conj(L[r][c], L[q][c]), y2));
-      if (threadIdx.x == 0) {
-        // thread 0 just produced the pivot of column c + 1
-        df d = L[c + 1][c + 1].re;
-        if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
-        const df y = df_rsqrt(d);
-        L[c + 1][c + 1] = cdf_make(df_mul(d, y), zero);
+    const df y = df_rsqrt1(d);
+    if (lane == 0) {
+      L[0][0].re = d;
+      yv[0] = y;
+      y2v[0] = df_mul(y, y);
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < NB - 1; ++c) {
+    if (pivot_warp) {
+      // (c+1, c+1) -= |a_{c+1,c}|^2 / d_c, then the pivot of column c + 1
+      const cdf a = L[c + 1][c];
+      const df m2 = df_add_sloppy(df_mul(a.re, a.re), df_mul(a.im, a.im));
+      df d = df_add_sloppy(L[c + 1][c + 1].re, df_neg(df_mul(m2, y2v[c])));
+      if (!(d.h > 0.f)) {
+        if (lane == 0) set_flag(status, ST_CHOL);
+        d = one;
+      }
+      const df y = df_rsqrt1(d);
+      if (lane == 0) {
+        L[c + 1][c + 1].re = d;
         yv[c + 1] = y;
-        y2b[(c + 1) & 1] = df_mul(y, y);
+        y2v[c + 1] = df_mul(y, y);
+      }
+    } else {
+      const df y2 = y2v[c];
+#pragma unroll
+      for (int i = 0; i < PF_PER; ++i) {
+        const int r = er[i], q = eq[i];
+        if (r >= 0 && q > c && !(q == c + 1 && r == c + 1))
+          L[r][q] = sub_outer(L[r][q], L[r][c], L[q][c], y2);
       }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
+  // scale: L_rc = a_rc / sqrt(d_c) below the diagonal, L_cc = sqrt(d_c) = d_c / sqrt(d_c)
+  for (int e = tid; e < NB * NB; e += PF_THREADS) {
+    const int r = e / NB, c = e % NB;
+    if (r > c) L[r][c] = cdf_scale(L[r][c], yv[c]);
+    else if (r == c) L[r][c] = cdf_make(df_mul(L[c][c].re, yv[c]), zero);
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += PF_THREADS) {
     const int r = e / NB, c = e % NB;
     if (c <= r && r0 + r < N && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = st4(L[r][c]);
   }
-  if (threadIdx.x < NB && r0 + threadIdx.x < N)
-    inv[r0 + threadIdx.x] = make_float2(yv[threadIdx.x].h, yv[threadIdx.x].l);
+  if (tid < NB && r0 + tid < N) inv[r0 + tid] = make_float2(yv[tid].h, yv[tid].l);
+  // D = L^{-1}: column j solves L d = e_j; lane r owns row r, final at step k = r
+  const int j0 = warp, j1 = warp + PF_THREADS / 32;
+  cacc acc0 = cacc_zero(), acc1 = cacc_zero();
+  cdf d0 = czero(), d1 = czero();
+  for (int k = 0; k < NB; ++k) {
+    const df yk = yv[k];
+    const cdf lk = L[lane][k];
+    if (k >= j0) {
+      const cdf v = cdf_scale(cdf_sub(cdf_make(k == j0 ? one : zero, zero), cacc_val(acc0)), yk);
+      const cdf b = shfl_cdf(v, k);
+      if (lane == k) d0 = b;
+      if (lane > k) cacc_mul(acc0, lk, b);
+    }
+    if (k >= j1) {
+      const cdf v = cdf_scale(cdf_sub(cdf_make(k == j1 ? one : zero, zero), cacc_val(acc1)), yk);
+      const cdf b = shfl_cdf(v, k);
+      if (lane == k) d1 = b;
+      if (lane > k) cacc_mul(acc1, lk, b);
+    }
+  }
+  if (r0 + lane < N) {
+    float4* Dr = D + ((size_t)jb * NB + lane) * NB;
+    Dr[j0] = st4(d0);
+    Dr[j1] = st4(d1);
+  }
 }
 
 // ---------------------------------------------------------------------------- panel solve
 
-constexpr int TR_WARPS = 8;
+// L_ij = A_ij L_jj^{-H} = A_ij D_jj^H for the rows below the diagonal block: 8 rows per CTA, one
+// output per thread, compensated dot products of length 32 (no dependency chain).
+constexpr int TS_ROWS = 8;
 
-__global__ void __launch_bounds__(TR_WARPS * 32) k_trsm_df(int N, Batch mb, int jb) {
-  __shared__ cdf Ls[NB][NB + 1];
-  __shared__ df ys[NB];
-  float4* A = mb.m[blockIdx.y];
-  const float2* inv = mb.inv[blockIdx.y];
+__global__ void __launch_bounds__(TS_ROWS * 32) k_trsm_gemm_df(int N, Batch mb, int jb) {
+  __shared__ cdf Ar[TS_ROWS][NB + 1];
+  __shared__ cdf Ds[NB][NB + 1];
+  float4* A = pick2(mb.m, blockIdx.y);
+  const float4* D = pick2(mb.D, blockIdx.y);
   const int c0 = jb * NB;
+  const int row0 = (jb + 1) * NB + blockIdx.x * TS_ROWS;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
-    cdf l = czero();
-    if (c < r && c0 + r < N && c0 + c < N) l = ld4(A[(size_t)(c0 + r) * N + c0 + c]);
-    Ls[r][c] = l;
+    Ds[r][c] = (c0 + r < N) ? ld4(D[((size_t)jb * NB + r) * NB + c]) : czero();
   }
-  if (threadIdx.x < NB) {
-    const float2 v = (c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : make_float2(1.f, 0.f);
-    ys[threadIdx.x] = df_make(v.x, v.y);
+  for (int e = threadIdx.x; e < TS_ROWS * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Ar[r][c] = (row0 + r < N && c0 + c < N) ? ld4(A[(size_t)(row0 + r) * N + c0 + c]) : czero();
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = (jb + 1) * NB + blockIdx.x * TR_WARPS + warp;
-  if (row >= N) return;
-  const bool cok = c0 + lane < N;
-  cdf a = cok ? ld4(A[(size_t)row * N + c0 + lane]) : czero();
-#pragma unroll 4
-  for (int m = 0; m < NB; ++m) {
-    const cdf xs = cdf_scale(a, ys[m]);
-    cdf x;
-    x.re.h = __shfl_sync(0xffffffffu, xs.re.h, m);
-    x.re.l = __shfl_sync(0xffffffffu, xs.re.l, m);
-    x.im.h = __shfl_sync(0xffffffffu, xs.im.h, m);
-    x.im.l = __shfl_sync(0xffffffffu, xs.im.l, m);
-    if (lane == m) a = x;
-    else if (lane > m) a = cdf_sub(a, cdf_mul_conj(x, Ls[lane][m]));
-  }
-  if (cok) A[(size_t)row * N + c0 + lane] = st4(a);
+  const int rr = threadIdx.x >> 5, c = threadIdx.x & 31;
+  cacc acc = cacc_zero();
+#pragma unroll 8
+  for (int m = 0; m < NB; ++m) cacc_mulc(acc, Ar[rr][m], Ds[c][m]);
+  if (row0 + rr < N && c0 + c < N) A[(size_t)(row0 + rr) * N + c0 + c] = st4(cacc_val(acc));
 }
 
 // ---------------------------------------------------------------------------- trailing update
@@ -230,38 +297,61 @@ __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
   I = t - Jc * (Jc + 1) / 2;
 }
 
+// a += x y for double-float reals (Dot2 step on the high parts, cross terms in FP32)
+__device__ __forceinline__ void acc_prod_df(acc2& a, df x, df y) {
+  acc_prod(a, x.h, y.h);
+  acc_small(a, DF_FMA(x.h, y.l, DF_MUL(x.l, y.h)));
+}
+__device__ __forceinline__ acc2 acc_neg(acc2 a) { a.s = -a.s; a.c = -a.c; return a; }
+
 // A_rc -= L_rb L_cb^H for jb < c <= r; compensated dot products of length 32 on the FP32 pipes.
+// Each complex product x conj(w) takes three real products (Karatsuba):
+//   P1 = xr wr, P2 = xi wi, P3 = (xr + xi)(wr - wi);  re = P1 + P2,  im = P3 - P1 + P2,
+// so the row operands are kept as (re, im, re + im) planes and the column operands, transposed
+// for conflict-free reads, as (re, im, re - im).  The error stays bounded relative to |x| |w|.
 __global__ void __launch_bounds__(256) k_herk_df(int N, Batch mb, int jb) {
-  __shared__ cdf Lr[NB][NB + 1];
-  __shared__ cdf Lc[NB][NB + 1];
-  float4* A = mb.m[blockIdx.y];
+  __shared__ df Rp[3][NB][NB];    // [plane][row][k]
+  __shared__ df Cp[3][NB][NB];    // [plane][k][col]
+  float4* A = pick2(mb.m, blockIdx.y);
   int I, J;
   tri_index(blockIdx.x, I, J);
   const int cb = jb + 1 + I, rb = jb + 1 + J;
   const int k0 = jb * NB;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, m = e % NB;
-    cdf a = czero(), b = czero();
+    cdf a = czero();
     if (rb * NB + r < N && k0 + m < N) a = ld4(A[(size_t)(rb * NB + r) * N + k0 + m]);
-    if (cb * NB + r < N && k0 + m < N) b = ld4(A[(size_t)(cb * NB + r) * N + k0 + m]);
-    Lr[r][m] = a;
-    Lc[r][m] = b;
+    Rp[0][r][m] = a.re;
+    Rp[1][r][m] = a.im;
+    Rp[2][r][m] = df_add_sloppy(a.re, a.im);
+    // transposed walk for the column tile: conflict-free shared-memory stores
+    const int m2 = e / NB, r2 = e % NB;
+    cdf b = czero();
+    if (cb * NB + r2 < N && k0 + m2 < N) b = ld4(A[(size_t)(cb * NB + r2) * N + k0 + m2]);
+    Cp[0][m2][r2] = b.re;
+    Cp[1][m2][r2] = b.im;
+    Cp[2][m2][r2] = df_add_sloppy(b.re, df_neg(b.im));
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  cacc acc[2][2];
+  acc2 acc[3][2][2];
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
+  for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int c = 0; c < 2; ++c) acc[r][c] = cacc_zero();
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) acc[p][r][c] = acc_zero();
 #pragma unroll 4
   for (int m = 0; m < NB; ++m) {
-    const cdf a0 = Lr[ty][m], a1 = Lr[ty + 16][m];
-    const cdf b0 = Lc[tx][m], b1 = Lc[tx + 16][m];
-    cacc_mulc(acc[0][0], a0, b0);
-    cacc_mulc(acc[0][1], a0, b1);
-    cacc_mulc(acc[1][0], a1, b0);
-    cacc_mulc(acc[1][1], a1, b1);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const df a0 = Rp[p][ty][m], a1 = Rp[p][ty + 16][m];
+      const df b0 = Cp[p][m][tx], b1 = Cp[p][m][tx + 16];
+      acc_prod_df(acc[p][0][0], a0, b0);
+      acc_prod_df(acc[p][0][1], a0, b1);
+      acc_prod_df(acc[p][1][0], a1, b0);
+      acc_prod_df(acc[p][1][1], a1, b1);
+    }
   }
 #pragma unroll
   for (int r = 0; r < 2; ++r)
@@ -269,49 +359,12 @@ __global__ void __launch_bounds__(256) k_herk_df(int N, Batch mb, int jb) {
     for (int c = 0; c < 2; ++c) {
       const int gr = rb * NB + ty + 16 * r, gc = cb * NB + tx + 16 * c;
       if (gr < N && gc < N && gc <= gr) {
+        const df re = acc_val(acc_merge(acc[0][r][c], acc[1][r][c]));
+        const df im = acc_val(acc_merge(acc_merge(acc[2][r][c], acc_neg(acc[0][r][c])), acc[1][r][c]));
         float4* p = A + (size_t)gr * N + gc;
-        *p = st4(cdf_sub(ld4(*p), cacc_val(acc[r][c])));
+        *p = st4(cdf_sub(ld4(*p), cdf_make(re, im)));
       }
     }
-}
-
-// ---------------------------------------------------------------------------- diagonal inverses
-
-__global__ void __launch_bounds__(128) k_trtri_df(int N, Batch mb) {
-  __shared__ cdf Ls[NB][NB + 1];
-  __shared__ cdf Dm[NB][NB + 1];
-  __shared__ df ys[NB];
-  const float4* A = mb.m[blockIdx.y];
-  const float2* inv = mb.inv[blockIdx.y];
-  float4* D = mb.D[blockIdx.y];
-  const int jb = blockIdx.x, r0 = jb * NB;
-  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    cdf l = czero();
-    if (c < r && r0 + r < N && r0 + c < N) l = ld4(A[(size_t)(r0 + r) * N + r0 + c]);
-    Ls[r][c] = l;
-    Dm[r][c] = cdf_make(r == c ? one : zero, zero);
-  }
-  if (threadIdx.x < NB) {
-    const float2 v = (r0 + threadIdx.x < N) ? inv[r0 + threadIdx.x] : make_float2(1.f, 0.f);
-    ys[threadIdx.x] = df_make(v.x, v.y);
-  }
-  __syncthreads();
-  for (int k = 0; k < NB; ++k) {
-    if (threadIdx.x <= k) Dm[k][threadIdx.x] = cdf_scale(Dm[k][threadIdx.x], ys[k]);
-    __syncthreads();
-    const int rows = NB - 1 - k, cols = k + 1;
-    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-      const int r = k + 1 + e / cols, c = e % cols;
-      Dm[r][c] = cdf_sub(Dm[r][c], cdf_mul(Ls[r][k], Dm[k][c]));
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    if (r0 + r < N) D[((size_t)jb * NB + r) * NB + c] = st4(Dm[r][c]);
-  }
 }
 
 // ---------------------------------------------------------------------------- triangular solves
@@ -332,14 +385,6 @@ __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-__device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
-  cdf r;
-  r.re.h = __shfl_sync(0xffffffffu, v.re.h, src);
-  r.re.l = __shfl_sync(0xffffffffu, v.re.l, src);
-  r.im.h = __shfl_sync(0xffffffffu, v.im.h, src);
-  r.im.l = __shfl_sync(0xffffffffu, v.im.l, src);
-  return r;
-}
 __device__ __forceinline__ cdf ldcg4(const float4* p) { return ld4(__ldcg(p)); }
 
 // Forward solve L z = y (z published as double-floats, consumers wait on per-block flags).
@@ -836,18 +881,17 @@ int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, 
   const int T = (N + NB - 1) / NB;
   int launches = 0;
   for (int jb = 0; jb < T; ++jb) {
-    k_potrf_df<<<dim3(1, nbatch), PF_THREADS, 0, s>>>(N, mb, jb, status);
+    k_potrf_inv_df<<<dim3(1, nbatch), PF_THREADS, 0, s>>>(N, mb, jb, status);
     ++launches;
     const int rest = T - jb - 1;
     if (rest > 0) {
       const int rows = N - (jb + 1) * NB;
-      k_trsm_df<<<dim3((rows + TR_WARPS - 1) / TR_WARPS, nbatch), TR_WARPS * 32, 0, s>>>(N, mb, jb);
+      k_trsm_gemm_df<<<dim3((rows + TS_ROWS - 1) / TS_ROWS, nbatch), TS_ROWS * 32, 0, s>>>(N, mb, jb);
       k_herk_df<<<dim3(rest * (rest + 1) / 2, nbatch), 256, 0, s>>>(N, mb, jb);
       launches += 2;
     }
   }
-  k_trtri_df<<<dim3(T, nbatch), 128, 0, s>>>(N, mb);
-  return launches + 1;
+  return launches;
 }
 
 void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y, void* work,

@@ -15,6 +15,7 @@ HDR = os.path.join(ROOT, "paper_1805_11169_gb300", "csrc", "df64.cuh")
 PROG = r'''
 #include <cstdio>
 #include <cstdlib>
+#include <cmath>
 #include "df64.cuh"
 using namespace icwf;
 int main(int argc, char** argv) {
@@ -26,6 +27,9 @@ int main(int argc, char** argv) {
     else if (op[0] == 's') r = df_sub(x, y);
     else if (op[0] == 'm') r = df_mul(x, y);
     else if (op[0] == 'r') r = df_rsqrt(x);
+    else if (op[0] == 'q') r = df_rsqrt1(x);
+    else if (op[0] == 'Q') r = df_rsqrt_refine(x, (float)(1.0 / sqrt((double)x.h)) * (float)b);
+    else if (op[0] == 'p') r = df_add_sloppy(x, y);
     else r = x;   // 'c': conversion round trip
     printf("%a %a\n", (double)r.h, (double)r.l);
   }
@@ -63,7 +67,11 @@ def test_df64_operations_have_48_bit_accuracy(prog):
     for _ in range(400):
         a = rnd.uniform(-1, 1) * 10 ** rnd.uniform(-6, 2)
         b = rnd.uniform(-1, 1) * 10 ** rnd.uniform(-6, 2)
-        cases += [("a", a, b), ("s", a, b), ("m", a, b), ("r", abs(a), 0.0), ("c", a, 0.0)]
+        cases += [("a", a, b), ("s", a, b), ("m", a, b), ("r", abs(a), 0.0), ("c", a, 0.0),
+                  ("q", abs(a), 0.0), ("p", a, b)]
+        # the device's FP32 reciprocal square root is not correctly rounded: seeds off by up to
+        # a few units in the last place must refine just as well
+        cases.append(("Q", abs(a), 1.0 + rnd.choice([-4, -2, -1, 1, 2, 4]) * 2.0 ** -23))
     res = run(prog, cases)
     # exact value of the df inputs (each input is first rounded to a df, ~48 bits)
     def df_exact(x):
@@ -74,16 +82,16 @@ def test_df64_operations_have_48_bit_accuracy(prog):
     worst = 0.0
     for (op, a, b), r in zip(cases, res):
         x, y = df_exact(a), df_exact(b)
-        if op == "a":
-            ref = x + y
-            scale = abs(x) + abs(y)
-        elif op == "s":
+        if op == "s":
             ref = x - y
             scale = abs(x) + abs(y)
         elif op == "m":
             ref = x * y
             scale = abs(ref)
-        elif op == "r":
+        elif op in ("a", "p"):
+            ref = x + y
+            scale = abs(x) + abs(y)
+        elif op in ("r", "q", "Q"):
             ref = Fraction(1) / Fraction(float(x) ** 0.5)   # reference to double accuracy
             scale = abs(ref)
         else:
@@ -91,7 +99,7 @@ def test_df64_operations_have_48_bit_accuracy(prog):
         if scale == 0:
             continue
         err = float(abs(r - ref) / scale)
-        tol = 2.0 ** -44 if op != "r" else 2.0 ** -43
+        tol = 2.0 ** -44 if op not in ("r", "q", "Q") else 2.0 ** -43
         worst = max(worst, err)
         assert err < tol, (op, a, b, err)
     assert worst > 0.0
