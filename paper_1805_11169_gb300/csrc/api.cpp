@@ -82,6 +82,7 @@ struct icwf_ctx {
   double *invL[2] = {nullptr, nullptr}, *invLh = nullptr;   // reciprocal Cholesky pivots
   double2 *DL[2] = {nullptr, nullptr}, *DLh = nullptr;       // inverted 32 x 32 diagonal blocks
   unsigned *flags = nullptr, *tickets = nullptr;
+  unsigned* cctl = nullptr;                                  // blocked-factorisation tickets/flags
   int* status = nullptr;
   int cur = 0;
   unsigned epoch = 0;
@@ -285,7 +286,7 @@ void factor(icwf_ctx* h, int n, const double2* const* S0, const double2* const* 
     void* a[2] = {dst[0], n > 1 ? dst[1] : dst[0]};
     void* iv[2] = {inv[0], n > 1 ? inv[1] : inv[0]};
     void* dd[2] = {D[0], n > 1 ? D[1] : D[0]};
-    h->launches += launch_cholesky_df(h->N, a, iv, dd, n, h->status, h->stream);
+    h->launches += launch_cholesky_df(h->N, a, iv, dd, n, h->cctl, h->status, h->stream);
   } else {
     h->launches += launch_cholesky(h->N, dst, inv, D, n, h->status, h->stream);
   }
@@ -553,7 +554,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
       NN * 16 * 7,         // S[2], H[2], L[2], Lh
       (size_t)N * 8, (size_t)N * 8, (size_t)N * 8,   // reciprocal pivots of L[2], Lh
       (size_t)N * 512, (size_t)N * 512, (size_t)N * 512,   // inverted diagonal blocks
-      (size_t)2 * nblk * 4 + 64, 64 * 4};
+      (size_t)2 * nblk * 4 + 64, chol_ctl_words(N) * sizeof(unsigned), 64 * 4};
   size_t total = 0;
   for (size_t b : sizes) total += align256(b);
   if (h->mixed) {
@@ -608,6 +609,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   h->DLh = (double2*)a.take((size_t)N * 512);
   h->flags = (unsigned*)a.take((size_t)2 * nblk * 4 + 64);
   h->tickets = h->flags + 2 * nblk;
+  h->cctl = (unsigned*)a.take(chol_ctl_words(N) * sizeof(unsigned));
   h->status = (int*)a.take(64 * 4);
   if (h->mixed) h->tc_scratch = a.take(h->tc_scratch_bytes);
   if (!h->status || (h->mixed && !h->tc_scratch)) {

@@ -106,8 +106,11 @@ void launch_chol_solve(int N, const double2* L, const double2* D, const double2*
 // double-float reciprocal pivots (8 bytes each); y and out are complex128.
 void launch_shift_mix_df(int N, const double2* S0, const double2* S1, double eps, double theta,
                          void* A, cudaStream_t s);
+// One launch per block column with look-ahead; ctl holds chol_ctl_words(N) words of ticket and
+// flag state (the launcher zeroes it).
 int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, int nbatch,
-                       int* status, cudaStream_t s);
+                       unsigned* ctl, int* status, cudaStream_t s);
+size_t chol_ctl_words(int N);
 void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y, void* work,
                           double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
                           unsigned epoch, int* status, cudaStream_t s);

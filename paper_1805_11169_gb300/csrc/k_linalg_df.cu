@@ -128,167 +128,6 @@ __global__ void k_shift_mix_df(int N, const double2* __restrict__ S0, const doub
   }
 }
 
-// ---------------------------------------------------------------------------- diagonal factor
-
-constexpr int PF_THREADS = 512;                                 // 15 update warps + 1 pivot warp
-constexpr int PF_WORKERS = PF_THREADS - 32;
-constexpr int PF_PAIRS = NB * (NB - 1) / 2;                     // (r, q), 1 <= q <= r < 32
-constexpr int PF_PER = (PF_PAIRS + PF_WORKERS - 1) / PF_WORKERS;
-
-// z - (x conj(w)) s with sloppy double-float additions (error relative to the operands' sizes)
-__device__ __forceinline__ cdf sub_outer(cdf z, cdf x, cdf w, df s) {
-  const df re = df_add_sloppy(df_mul(x.re, w.re), df_mul(x.im, w.im));
-  const df im = df_add_sloppy(df_mul(x.im, w.re), df_neg(df_mul(x.re, w.im)));
-  return cdf_make(df_add_sloppy(z.re, df_neg(df_mul(re, s))),
-                  df_add_sloppy(z.im, df_neg(df_mul(im, s))));
-}
-
-// Factor and invert one 32 x 32 diagonal block: L_jj L_jj^H = A_jj and D_jj = L_jj^{-1}.
-// Right-looking with unscaled columns: step c subtracts a_rc conj(a_qc) / d_c from the trailing
-// block (d_c the pivot) and columns are scaled by 1/sqrt(d_c) at the end.  A dedicated warp
-// computes the next pivot during each step (it applies column c to element (c+1, c+1) itself and
-// takes the reciprocal square root), so a column costs one barrier and the pivot chain runs
-// beside the update.  The inverse is then formed by forward substitution of the 32 unit vectors,
-// two columns per warp, with compensated (Dot2) accumulation.
-__global__ void __launch_bounds__(PF_THREADS) k_potrf_inv_df(int N, Batch mb, int jb, int* status) {
-  __shared__ cdf L[NB][NB + 1];
-  __shared__ df yv[NB];     // 1 / sqrt(d_c)
-  __shared__ df y2v[NB];    // 1 / d_c
-  float4* A = pick2(mb.m, blockIdx.y);
-  float2* inv = pick2(mb.inv, blockIdx.y);
-  float4* D = pick2(mb.D, blockIdx.y);
-  const int r0 = jb * NB;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool pivot_warp = warp == PF_THREADS / 32 - 1;
-  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
-  for (int e = tid; e < NB * NB; e += PF_THREADS) {
-    const int r = e / NB, c = e % NB;
-    cdf v = cdf_make(r == c ? one : zero, zero);
-    if (c <= r && r0 + r < N && r0 + c < N) v = ld4(A[(size_t)(r0 + r) * N + r0 + c]);
-    L[r][c] = v;
-  }
-  // this worker's elements (r, q), 1 <= q <= r, packed as e = r (r - 1) / 2 + q - 1
-  int er[PF_PER], eq[PF_PER];
-#pragma unroll
-  for (int i = 0; i < PF_PER; ++i) {
-    const int e = tid + i * PF_WORKERS;
-    int r = 1;
-    while (r * (r + 1) / 2 <= e) ++r;
-    er[i] = (!pivot_warp && e < PF_PAIRS) ? r : -1;
-    eq[i] = e - r * (r - 1) / 2 + 1;
-  }
-  __syncthreads();
-  if (pivot_warp) {
-    df d = L[0][0].re;
-    if (!(d.h > 0.f)) {
-      if (lane == 0) set_flag(status, ST_CHOL);
-      d = one;
-    }
-    const df y = df_rsqrt1(d);
-    if (lane == 0) {
-      L[0][0].re = d;
-      yv[0] = y;
-      y2v[0] = df_mul(y, y);
-    }
-  }
-  __syncthreads();
-  for (int c = 0; c < NB - 1; ++c) {
-    if (pivot_warp) {
-      // (c+1, c+1) -= |a_{c+1,c}|^2 / d_c, then the pivot of column c + 1
-      const cdf a = L[c + 1][c];
-      const df m2 = df_add_sloppy(df_mul(a.re, a.re), df_mul(a.im, a.im));
-      df d = df_add_sloppy(L[c + 1][c + 1].re, df_neg(df_mul(m2, y2v[c])));
-      if (!(d.h > 0.f)) {
-        if (lane == 0) set_flag(status, ST_CHOL);
-        d = one;
-      }
-      const df y = df_rsqrt1(d);
-      if (lane == 0) {
-        L[c + 1][c + 1].re = d;
-        yv[c + 1] = y;
-        y2v[c + 1] = df_mul(y, y);
-      }
-    } else {
-      const df y2 = y2v[c];
-#pragma unroll
-      for (int i = 0; i < PF_PER; ++i) {
-        const int r = er[i], q = eq[i];
-        if (r >= 0 && q > c && !(q == c + 1 && r == c + 1))
-          L[r][q] = sub_outer(L[r][q], L[r][c], L[q][c], y2);
-      }
-    }
-    __syncthreads();
-  }
-  // scale: L_rc = a_rc / sqrt(d_c) below the diagonal, L_cc = sqrt(d_c) = d_c / sqrt(d_c)
-  for (int e = tid; e < NB * NB; e += PF_THREADS) {
-    const int r = e / NB, c = e % NB;
-    if (r > c) L[r][c] = cdf_scale(L[r][c], yv[c]);
-    else if (r == c) L[r][c] = cdf_make(df_mul(L[c][c].re, yv[c]), zero);
-  }
-  __syncthreads();
-  for (int e = tid; e < NB * NB; e += PF_THREADS) {
-    const int r = e / NB, c = e % NB;
-    if (c <= r && r0 + r < N && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = st4(L[r][c]);
-  }
-  if (tid < NB && r0 + tid < N) inv[r0 + tid] = make_float2(yv[tid].h, yv[tid].l);
-  // D = L^{-1}: column j solves L d = e_j; lane r owns row r, final at step k = r
-  const int j0 = warp, j1 = warp + PF_THREADS / 32;
-  cacc acc0 = cacc_zero(), acc1 = cacc_zero();
-  cdf d0 = czero(), d1 = czero();
-  for (int k = 0; k < NB; ++k) {
-    const df yk = yv[k];
-    const cdf lk = L[lane][k];
-    if (k >= j0) {
-      const cdf v = cdf_scale(cdf_sub(cdf_make(k == j0 ? one : zero, zero), cacc_val(acc0)), yk);
-      const cdf b = shfl_cdf(v, k);
-      if (lane == k) d0 = b;
-      if (lane > k) cacc_mul(acc0, lk, b);
-    }
-    if (k >= j1) {
-      const cdf v = cdf_scale(cdf_sub(cdf_make(k == j1 ? one : zero, zero), cacc_val(acc1)), yk);
-      const cdf b = shfl_cdf(v, k);
-      if (lane == k) d1 = b;
-      if (lane > k) cacc_mul(acc1, lk, b);
-    }
-  }
-  if (r0 + lane < N) {
-    float4* Dr = D + ((size_t)jb * NB + lane) * NB;
-    Dr[j0] = st4(d0);
-    Dr[j1] = st4(d1);
-  }
-}
-
-// ---------------------------------------------------------------------------- panel solve
-
-// L_ij = A_ij L_jj^{-H} = A_ij D_jj^H for the rows below the diagonal block: 8 rows per CTA, one
-// output per thread, compensated dot products of length 32 (no dependency chain).
-constexpr int TS_ROWS = 8;
-
-__global__ void __launch_bounds__(TS_ROWS * 32) k_trsm_gemm_df(int N, Batch mb, int jb) {
-  __shared__ cdf Ar[TS_ROWS][NB + 1];
-  __shared__ cdf Ds[NB][NB + 1];
-  float4* A = pick2(mb.m, blockIdx.y);
-  const float4* D = pick2(mb.D, blockIdx.y);
-  const int c0 = jb * NB;
-  const int row0 = (jb + 1) * NB + blockIdx.x * TS_ROWS;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    Ds[r][c] = (c0 + r < N) ? ld4(D[((size_t)jb * NB + r) * NB + c]) : czero();
-  }
-  for (int e = threadIdx.x; e < TS_ROWS * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    Ar[r][c] = (row0 + r < N && c0 + c < N) ? ld4(A[(size_t)(row0 + r) * N + c0 + c]) : czero();
-  }
-  __syncthreads();
-  const int rr = threadIdx.x >> 5, c = threadIdx.x & 31;
-  cacc acc = cacc_zero();
-#pragma unroll 8
-  for (int m = 0; m < NB; ++m) cacc_mulc(acc, Ar[rr][m], Ds[c][m]);
-  if (row0 + rr < N && c0 + c < N) A[(size_t)(row0 + rr) * N + c0 + c] = st4(cacc_val(acc));
-}
-
-// ---------------------------------------------------------------------------- trailing update
-
 __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
   int Jc = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
   while (Jc * (Jc + 1) / 2 > t) --Jc;
@@ -297,37 +136,110 @@ __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
   I = t - Jc * (Jc + 1) / 2;
 }
 
+// ---------------------------------------------------------------------------- blocked factorisation
+//
+// Right-looking blocked Cholesky with one launch per block column and a look-ahead: launch li
+// applies panel li - 1 to the trailing matrix and, in the same launch, factors diagonal block li
+// and solves panel li.  Its CTAs take tickets in dependency order
+//   [3 quadrant updates of diagonal block li] [diagonal factor li] [trailing tiles right of
+//   block column li] [panel-li slabs of 8 rows],
+// and wait (bounded) only for tasks with smaller tickets, which are already running: the diagonal
+// factor waits for its three quadrants, the panel slabs for the diagonal factor.  So the chain
+// quadrants -> factor -> slabs overlaps the bulk of the trailing update, and the factor of block
+// li + 1 starts as soon as launch li + 1 does.  All arithmetic is double-float with compensated
+// (Dot2) accumulation; complex products in the updates use three real products (Karatsuba).
+
+constexpr int CS_THREADS = 256;
+constexpr int TS_ROWS = 8;                    // panel rows per slab task
+constexpr unsigned CS_WAIT_LIMIT = 1u << 24;
+constexpr int CS_SMEM = 6 * NB * NB * 8;      // largest task: trailing tile, 6 double-float planes
+
+__device__ __forceinline__ cdf ldcg4(const float4* p) { return ld4(__ldcg(p)); }
+__device__ __forceinline__ cdf cdf_sub_sloppy(cdf a, cdf b) {
+  return cdf_make(df_add_sloppy(a.re, df_neg(b.re)), df_add_sloppy(a.im, df_neg(b.im)));
+}
 // a += x y for double-float reals (Dot2 step on the high parts, cross terms in FP32)
 __device__ __forceinline__ void acc_prod_df(acc2& a, df x, df y) {
   acc_prod(a, x.h, y.h);
   acc_small(a, DF_FMA(x.h, y.l, DF_MUL(x.l, y.h)));
 }
 __device__ __forceinline__ acc2 acc_neg(acc2 a) { a.s = -a.s; a.c = -a.c; return a; }
+// Karatsuba: x conj(w) from P1 = xr wr, P2 = xi wi, P3 = (xr + xi)(wr - wi)
+__device__ __forceinline__ cdf kara_val(acc2 p1, acc2 p2, acc2 p3) {
+  return cdf_make(acc_val(acc_merge(p1, p2)), acc_val(acc_merge(acc_merge(p3, acc_neg(p1)), p2)));
+}
 
-// A_rc -= L_rb L_cb^H for jb < c <= r; compensated dot products of length 32 on the FP32 pipes.
-// Each complex product x conj(w) takes three real products (Karatsuba):
-//   P1 = xr wr, P2 = xi wi, P3 = (xr + xi)(wr - wi);  re = P1 + P2,  im = P3 - P1 + P2,
-// so the row operands are kept as (re, im, re + im) planes and the column operands, transposed
-// for conflict-free reads, as (re, im, re - im).  The error stays bounded relative to |x| |w|.
-__global__ void __launch_bounds__(256) k_herk_df(int N, Batch mb, int jb) {
-  __shared__ df Rp[3][NB][NB];    // [plane][row][k]
-  __shared__ df Cp[3][NB][NB];    // [plane][k][col]
-  float4* A = pick2(mb.m, blockIdx.y);
-  int I, J;
-  tri_index(blockIdx.x, I, J);
-  const int cb = jb + 1 + I, rb = jb + 1 + J;
+__device__ __forceinline__ bool cs_wait(const unsigned* f, unsigned target, int* status) {
+  for (unsigned it = 0; it < CS_WAIT_LIMIT; ++it) {
+    if (ld_acquire(f) >= target) return true;
+    if (it > 256) __nanosleep(128);
+  }
+  set_flag(status, ST_TIMEOUT);
+  return false;
+}
+// all of this CTA's global writes, then a release increment of *f
+__device__ __forceinline__ void cs_signal(unsigned* f) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(f, 1u);
+  }
+}
+
+// One output per thread of an R x C block (R C = 256): returns A[orow][ocol] - sum_k X[r][k] conj(Y[c][k])
+// with X = rows xrow0.., Y = rows yrow0.. of A over columns k0..k0+31.
+template <int R, int C>
+__device__ __forceinline__ cdf upd_one(const float4* A, int N, int xrow0, int yrow0, int k0,
+                                       int orow, int ocol, bool ok, unsigned char* smem) {
+  df(*Xp)[R][NB] = (df(*)[R][NB])smem;                        // [3][R][32]
+  df(*Yp)[NB][C] = (df(*)[NB][C])(smem + 3 * R * NB * 8);     // [3][32][C]
+  for (int e = threadIdx.x; e < R * NB; e += CS_THREADS) {
+    const int r = e / NB, k = e % NB;
+    cdf x = czero();
+    if (xrow0 + r < N && k0 + k < N) x = ldcg4(A + (size_t)(xrow0 + r) * N + k0 + k);
+    Xp[0][r][k] = x.re;
+    Xp[1][r][k] = x.im;
+    Xp[2][r][k] = df_add_sloppy(x.re, x.im);
+  }
+  for (int e = threadIdx.x; e < C * NB; e += CS_THREADS) {
+    const int k = e / C, c = e % C;
+    cdf y = czero();
+    if (yrow0 + c < N && k0 + k < N) y = ldcg4(A + (size_t)(yrow0 + c) * N + k0 + k);
+    Yp[0][k][c] = y.re;
+    Yp[1][k][c] = y.im;
+    Yp[2][k][c] = df_add_sloppy(y.re, df_neg(y.im));
+  }
+  __syncthreads();
+  const int r = threadIdx.x / C, c = threadIdx.x % C;
+  acc2 p1 = acc_zero(), p2 = acc_zero(), p3 = acc_zero();
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    acc_prod_df(p1, Xp[0][r][k], Yp[0][k][c]);
+    acc_prod_df(p2, Xp[1][r][k], Yp[1][k][c]);
+    acc_prod_df(p3, Xp[2][r][k], Yp[2][k][c]);
+  }
+  const cdf a = ok ? ldcg4(A + (size_t)orow * N + ocol) : czero();
+  __syncthreads();
+  return cdf_sub(a, kara_val(p1, p2, p3));
+}
+
+// Trailing tile (rb, cb), cb <= rb: A_rc -= L_r,jb L_c,jb^H, 2 x 2 outputs per thread.
+__device__ __forceinline__ void herk_tile(float4* A, int N, int jb, int rb, int cb,
+                                          unsigned char* smem) {
+  df(*Rp)[NB][NB] = (df(*)[NB][NB])smem;                      // [plane][row][k]
+  df(*Cp)[NB][NB] = (df(*)[NB][NB])(smem + 3 * NB * NB * 8);  // [plane][k][col]
   const int k0 = jb * NB;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+  for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
     const int r = e / NB, m = e % NB;
     cdf a = czero();
-    if (rb * NB + r < N && k0 + m < N) a = ld4(A[(size_t)(rb * NB + r) * N + k0 + m]);
+    if (rb * NB + r < N && k0 + m < N) a = ldcg4(A + (size_t)(rb * NB + r) * N + k0 + m);
     Rp[0][r][m] = a.re;
     Rp[1][r][m] = a.im;
     Rp[2][r][m] = df_add_sloppy(a.re, a.im);
     // transposed walk for the column tile: conflict-free shared-memory stores
     const int m2 = e / NB, r2 = e % NB;
     cdf b = czero();
-    if (cb * NB + r2 < N && k0 + m2 < N) b = ld4(A[(size_t)(cb * NB + r2) * N + k0 + m2]);
+    if (cb * NB + r2 < N && k0 + m2 < N) b = ldcg4(A + (size_t)(cb * NB + r2) * N + k0 + m2);
     Cp[0][m2][r2] = b.re;
     Cp[1][m2][r2] = b.im;
     Cp[2][m2][r2] = df_add_sloppy(b.re, df_neg(b.im));
@@ -359,12 +271,255 @@ __global__ void __launch_bounds__(256) k_herk_df(int N, Batch mb, int jb) {
     for (int c = 0; c < 2; ++c) {
       const int gr = rb * NB + ty + 16 * r, gc = cb * NB + tx + 16 * c;
       if (gr < N && gc < N && gc <= gr) {
-        const df re = acc_val(acc_merge(acc[0][r][c], acc[1][r][c]));
-        const df im = acc_val(acc_merge(acc_merge(acc[2][r][c], acc_neg(acc[0][r][c])), acc[1][r][c]));
         float4* p = A + (size_t)gr * N + gc;
-        *p = st4(cdf_sub(ld4(*p), cdf_make(re, im)));
+        *p = st4(cdf_sub(ldcg4(p), kara_val(acc[0][r][c], acc[1][r][c], acc[2][r][c])));
       }
     }
+}
+
+// Factor diagonal block jp in place: L L^H = A_jp,jp (lower triangle), reciprocal pivots to inv.
+// Warp 7 runs the pivot chain: at step s it takes column s+1 as left by step s-1 (all columns up to
+// s-1 applied), applies column s itself, forms the pivot d = a_{s+1,s+1}, y = 1/sqrt(d) (one
+// refinement step) and publishes l_{.,s+1} = a_{.,s+1} y.  Warps 0..6 own the entries of columns
+// >= 2 in column-descending order, so the entries that step s must update (columns >= s+2) are a
+// prefix of that order and idle warps skip the step; each entry keeps A and a compensated
+// accumulator of sum_k l_rk conj(l_qk) in registers, and the entries of column s+2 hand their
+// value to the pivot warp through a double-buffered shared-memory row.  One barrier per column.
+constexpr int PW_BULK = 7 * 32;
+constexpr int PW_PAIRS = (NB - 2) * (NB - 1) / 2;                  // entries of columns 2..31
+constexpr int PW_SLOTS = (PW_PAIRS + PW_BULK - 1) / PW_BULK;
+
+__device__ __forceinline__ void potrf_task(int N, float4* A, float2* inv, int jp, int* status,
+                                           unsigned char* smem) {
+  cdf* col = (cdf*)smem;                   // col[c * 32 + r] = l_rc, r >= c
+  cdf* pend = col + NB * NB;               // [2][32]: column handed to the pivot warp
+  df* yv = (df*)(pend + 2 * NB);           // 1 / sqrt(d_c)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = jp * NB;
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
+  auto load = [&](int r, int q) -> cdf {
+    if (r0 + r < N) return ldcg4(A + (size_t)(r0 + r) * N + r0 + q);
+    return cdf_make(r == q ? one : zero, zero);
+  };
+  if (warp == 7) {
+    // pivot warp: columns 0 and 1 straight from A
+    const cdf a0 = load(lane, 0);
+    cdf a1 = lane >= 1 ? load(lane, 1) : czero();
+    df d;
+    d.h = __shfl_sync(0xffffffffu, a0.re.h, 0);
+    d.l = __shfl_sync(0xffffffffu, a0.re.l, 0);
+    if (!(d.h > 0.f)) {
+      if (lane == 0) set_flag(status, ST_CHOL);
+      d = one;
+    }
+    const df y = df_rsqrt1(d);
+    col[lane] = lane == 0 ? cdf_make(df_mul(d, y), zero) : cdf_scale(a0, y);
+    if (lane == 0) yv[0] = y;
+    pend[NB + lane] = a1;                  // column 1, nothing applied yet (parity 1)
+  }
+  // bulk entries: column-descending order over columns 31..2, column q holds rows q..31
+  int er[PW_SLOTS], eq[PW_SLOTS];
+  cdf av[PW_SLOTS];
+  cacc acc[PW_SLOTS];
+#pragma unroll
+  for (int i = 0; i < PW_SLOTS; ++i) {
+    int e = threadIdx.x + i * PW_BULK, q = NB - 1;
+    while (q > 2 && e >= NB - q) { e -= NB - q; --q; }
+    const bool on = warp < 7 && threadIdx.x + i * PW_BULK < PW_PAIRS;
+    er[i] = on ? q + e : -1;
+    eq[i] = q;
+    av[i] = on ? load(q + e, q) : czero();
+    acc[i] = cacc_zero();
+  }
+  __syncthreads();
+  for (int s = 0; s < NB - 1; ++s) {
+    if (warp == 7) {
+      // column s+1: v = (value through column s-1) - l_{r,s} conj(l_{s+1,s}), then its pivot
+      const int c = s + 1;
+      const cdf w = pend[(c & 1) * NB + lane];
+      const cdf lr = col[s * NB + lane];
+      const cdf lq = col[s * NB + c];
+      const cdf v = cdf_sub_sloppy(w, cdf_mul_conj(lr, lq));
+      df d;
+      d.h = __shfl_sync(0xffffffffu, v.re.h, c);
+      d.l = __shfl_sync(0xffffffffu, v.re.l, c);
+      if (!(d.h > 0.f)) {
+        if (lane == 0) set_flag(status, ST_CHOL);
+        d = one;
+      }
+      const df y = df_rsqrt1(d);
+      if (lane > c) col[c * NB + lane] = cdf_scale(v, y);
+      else if (lane == c) col[c * NB + c] = cdf_make(df_mul(d, y), zero);
+      if (lane == 0) yv[c] = y;
+    } else if (warp * 32 < (NB - 2 - s) * (NB - 1 - s) / 2) {
+      // entries of columns >= s+2 (the first (30-s)(31-s)/2 of the order) take column s
+      const int nact = (NB - 2 - s) * (NB - 1 - s) / 2;
+      const cdf* cs = col + s * NB;
+#pragma unroll
+      for (int i = 0; i < PW_SLOTS; ++i) {
+        if (threadIdx.x + i * PW_BULK < nact) {
+          const int r = er[i], q = eq[i];
+          cacc_mulc(acc[i], cs[r], cs[q]);
+          if (q == s + 2) pend[(q & 1) * NB + r] = cdf_sub_sloppy(av[i], cacc_val(acc[i]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
+    const int q = e / NB, r = e % NB;
+    if (r >= q && r0 + r < N) A[(size_t)(r0 + r) * N + r0 + q] = st4(col[q * NB + r]);
+  }
+  if (threadIdx.x < NB && r0 + threadIdx.x < N)
+    inv[r0 + threadIdx.x] = make_float2(yv[threadIdx.x].h, yv[threadIdx.x].l);
+}
+
+// D = L^{-1} of diagonal block jp (final): column j solves L d = e_j by forward substitution,
+// warp w takes columns w, w+8, w+16, w+24, lane r row r, compensated accumulation.
+__device__ __forceinline__ void trtri_task(int N, const float4* A, const float2* inv, float4* D,
+                                           int jp, unsigned char* smem) {
+  cdf(*Ls)[NB + 1] = (cdf(*)[NB + 1])smem;
+  df* ys = (df*)(smem + NB * (NB + 1) * 16);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = jp * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
+    const int r = e / NB, c = e % NB;
+    Ls[r][c] = (c < r && r0 + r < N) ? ldcg4(A + (size_t)(r0 + r) * N + r0 + c) : czero();
+  }
+  if (threadIdx.x < NB) {
+    const float2 v = r0 + threadIdx.x < N ? __ldcg(inv + r0 + threadIdx.x) : make_float2(1.f, 0.f);
+    ys[threadIdx.x] = df_make(v.x, v.y);
+  }
+  __syncthreads();
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
+  cacc acc[4];
+  cdf dv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    acc[i] = cacc_zero();
+    dv[i] = czero();
+  }
+  for (int k = 0; k < NB; ++k) {
+    const df yk = ys[k];
+    const cdf lk = Ls[lane][k];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = warp + 8 * i;
+      if (k >= j) {
+        const cdf v = cdf_scale(cdf_sub(cdf_make(k == j ? one : zero, zero), cacc_val(acc[i])), yk);
+        const cdf b = shfl_cdf(v, k);
+        if (lane == k) dv[i] = b;
+        if (lane > k) cacc_mul(acc[i], lk, b);
+      }
+    }
+  }
+  if (r0 + lane < N) {
+    float4* Dr = D + ((size_t)jp * NB + lane) * NB;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Dr[warp + 8 * i] = st4(dv[i]);
+  }
+}
+
+__global__ void __launch_bounds__(CS_THREADS) k_chol_step_df(int N, Batch mb, int nb, int li,
+                                                            unsigned* ctl, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ unsigned s_t;
+  const int T = (N + NB - 1) / NB;
+  const int jp = li, jb = li - 1;
+  unsigned* diag = ctl + (T + 2) + 2 * li;     // [li][matrix]: finished quadrants
+  unsigned* pdone = ctl + 3 * (T + 2) + 2 * li;  // [li][matrix]: diagonal factor published
+  if (threadIdx.x == 0) s_t = atomicAdd(ctl + li, 1u);
+  __syncthreads();
+  int t = (int)s_t;
+  const int ndiag = (jb >= 0 && jp < T) ? 3 : 0;
+  const int rt = T - jb - 2;
+  const int nherk = (jb >= 0 && rt > 0) ? rt * (rt + 1) / 2 : 0;
+  const int rows = N - (jp + 1) * NB;
+  const int nslab = (jp < T && rows > 0) ? (rows + TS_ROWS - 1) / TS_ROWS : 0;
+  if (t < nb * ndiag) {
+    // quadrant (rh, ch) of diagonal block jp: A -= L_jp,jb L_jp,jb^H
+    const int m = t % nb, qd = t / nb;
+    const int rh = qd > 0 ? 1 : 0, ch = qd > 1 ? 1 : 0;
+    float4* A = pick2(mb.m, m);
+    const int r = threadIdx.x / 16, c = threadIdx.x % 16;
+    const int orow = jp * NB + rh * 16 + r, ocol = jp * NB + ch * 16 + c;
+    const bool ok = orow < N && ocol < N && (rh != ch || c <= r);
+    const cdf v = upd_one<16, 16>(A, N, jp * NB + rh * 16, jp * NB + ch * 16, jb * NB, orow, ocol,
+                                  ok, sm);
+    if (ok) A[(size_t)orow * N + ocol] = st4(v);
+    cs_signal(diag + m);
+    return;
+  }
+  t -= nb * ndiag;
+  const int npotrf = jp < T ? 1 : 0;
+  if (t < nb * npotrf) {
+    const int m = t;
+    if (ndiag > 0) {
+      if (threadIdx.x == 0) {
+        cs_wait(diag + m, 3u, status);
+        __threadfence();
+      }
+      __syncthreads();
+    }
+    potrf_task(N, pick2(mb.m, m), pick2(mb.inv, m), jp, status, sm);
+    cs_signal(pdone + m);
+    return;
+  }
+  t -= nb * npotrf;
+  const int ntrtri = jp >= 1 ? 1 : 0;
+  if (t < nb * ntrtri) {
+    // inverse of the previous diagonal block (final since the previous launch), for the solves
+    const int m = t;
+    trtri_task(N, pick2(mb.m, m), pick2(mb.inv, m), pick2(mb.D, m), jp - 1, sm);
+    return;
+  }
+  t -= nb * ntrtri;
+  if (t < nb * nherk) {
+    const int m = t % nb;
+    int I, J;
+    tri_index(t / nb, I, J);
+    herk_tile(pick2(mb.m, m), N, jb, jb + 2 + J, jb + 2 + I, sm);
+    return;
+  }
+  t -= nb * nherk;
+  if (t < nb * nslab) {
+    // panel slab: rows i0..i0+7 of block column jp.  a = A - L_i,jb L_jp,jb^H, then x L^H = a by
+    // substitution along the row (warp = row, lane = column): x_m = (a_m - sum_k<m x_k conj(L_mk)) / L_mm
+    const int m = t % nb, sl = t / nb;
+    float4* A = pick2(mb.m, m);
+    const float2* inv = pick2(mb.inv, m);
+    const int i0 = (jp + 1) * NB + sl * TS_ROWS;
+    const int r = threadIdx.x / NB, c = threadIdx.x % NB;
+    const bool ok = i0 + r < N;
+    cdf a;
+    if (jb >= 0) a = upd_one<TS_ROWS, NB>(A, N, i0, jp * NB, jb * NB, i0 + r, jp * NB + c, ok, sm);
+    else a = ok ? ldcg4(A + (size_t)(i0 + r) * N + jp * NB + c) : czero();
+    if (threadIdx.x == 0) {
+      cs_wait(pdone + m, 1u, status);
+      __threadfence();
+    }
+    __syncthreads();
+    cdf(*Ls)[NB + 1] = (cdf(*)[NB + 1])sm;                      // [32][33]
+    df* ys = (df*)(sm + NB * (NB + 1) * 16);
+    for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
+      const int rr = e / NB, cc = e % NB;
+      Ls[rr][cc] = cc < rr ? ldcg4(A + (size_t)(jp * NB + rr) * N + jp * NB + cc) : czero();
+    }
+    if (threadIdx.x < NB) {
+      const float2 v = __ldcg(inv + jp * NB + threadIdx.x);
+      ys[threadIdx.x] = df_make(v.x, v.y);
+    }
+    __syncthreads();
+    cacc s = cacc_zero();
+    cdf x = czero();
+    for (int k = 0; k < NB; ++k) {
+      const cdf v = cdf_scale(cdf_sub_sloppy(a, cacc_val(s)), ys[k]);
+      const cdf xk = shfl_cdf(v, k);
+      if (c == k) x = xk;
+      if (c > k) cacc_mulc(s, xk, Ls[c][k]);
+    }
+    if (ok) A[(size_t)(i0 + r) * N + jp * NB + c] = st4(x);
+  }
 }
 
 // ---------------------------------------------------------------------------- triangular solves
@@ -385,7 +540,6 @@ __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-__device__ __forceinline__ cdf ldcg4(const float4* p) { return ld4(__ldcg(p)); }
 
 // Forward solve L z = y (z published as double-floats, consumers wait on per-block flags).
 // Same schedule as the FP64 kernel: warps CW.. accumulate the older blocks, warps 0..CW-1 share the
@@ -869,7 +1023,7 @@ void launch_shift_mix_df(int N, const double2* S0, const double2* S1, double eps
 }
 
 int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, int nbatch,
-                       int* status, cudaStream_t s) {
+                       unsigned* ctl, int* status, cudaStream_t s) {
   using namespace dfs;
   Batch mb;
   for (int q = 0; q < 2; ++q) {
@@ -879,20 +1033,25 @@ int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, 
     mb.D[q] = (float4*)D[k];
   }
   const int T = (N + NB - 1) / NB;
-  int launches = 0;
-  for (int jb = 0; jb < T; ++jb) {
-    k_potrf_inv_df<<<dim3(1, nbatch), PF_THREADS, 0, s>>>(N, mb, jb, status);
-    ++launches;
-    const int rest = T - jb - 1;
-    if (rest > 0) {
-      const int rows = N - (jb + 1) * NB;
-      k_trsm_gemm_df<<<dim3((rows + TS_ROWS - 1) / TS_ROWS, nbatch), TS_ROWS * 32, 0, s>>>(N, mb, jb);
-      k_herk_df<<<dim3(rest * (rest + 1) / 2, nbatch), 256, 0, s>>>(N, mb, jb);
-      launches += 2;
-    }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_chol_step_df, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM);
+    attr = true;
   }
-  return launches;
+  cudaMemsetAsync(ctl, 0, chol_ctl_words(N) * sizeof(unsigned), s);
+  for (int li = 0; li <= T; ++li) {
+    const int jb = li - 1;
+    const int rt = T - jb - 2;
+    const int nherk = (jb >= 0 && rt > 0) ? rt * (rt + 1) / 2 : 0;
+    const int rows = N - (li + 1) * NB;
+    const int nslab = (li < T && rows > 0) ? (rows + TS_ROWS - 1) / TS_ROWS : 0;
+    const int per = (jb >= 0 && li < T ? 3 : 0) + (li < T ? 1 : 0) + (li >= 1 ? 1 : 0) + nherk + nslab;
+    k_chol_step_df<<<nbatch * per, CS_THREADS, CS_SMEM, s>>>(N, mb, nbatch, li, ctl, status);
+  }
+  return T + 2;
 }
+
+size_t chol_ctl_words(int N) { return (size_t)5 * ((N + dfs::NB - 1) / dfs::NB + 2); }
 
 void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y, void* work,
                           double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
