@@ -374,14 +374,19 @@ __device__ __forceinline__ void potrf_task(int N, float4* A, float2* inv, int jp
     inv[r0 + threadIdx.x] = make_float2(yv[threadIdx.x].h, yv[threadIdx.x].l);
 }
 
-// D = L^{-1} of diagonal block jp (final): column j solves L d = e_j by forward substitution,
-// warp w takes columns w, w+8, w+16, w+24, lane r row r, compensated accumulation.
+// D = L^{-1} of diagonal block jp (final), by 2 x 2 blocks of 16:
+//   D11 = L11^{-1}, D22 = L22^{-1} (forward substitution of the unit vectors, one column per
+//   half-warp, compensated accumulation), then D21 = -D22 (L21 D11) as two 16 x 16 products.
 __device__ __forceinline__ void trtri_task(int N, const float4* A, const float2* inv, float4* D,
                                            int jp, unsigned char* smem) {
-  cdf(*Ls)[NB + 1] = (cdf(*)[NB + 1])smem;
-  df* ys = (df*)(smem + NB * (NB + 1) * 16);
+  constexpr int H = NB / 2;
+  cdf(*Ls)[NB + 1] = (cdf(*)[NB + 1])smem;                                  // [32][33]
+  cdf(*Ds)[NB + 1] = (cdf(*)[NB + 1])(smem + NB * (NB + 1) * 16);           // [32][33]
+  cdf(*Ts)[H + 1] = (cdf(*)[H + 1])(smem + 2 * NB * (NB + 1) * 16);         // [16][17]
+  df* ys = (df*)(smem + 2 * NB * (NB + 1) * 16 + H * (H + 1) * 16);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = jp * NB;
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
   for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
     const int r = e / NB, c = e % NB;
     Ls[r][c] = (c < r && r0 + r < N) ? ldcg4(A + (size_t)(r0 + r) * N + r0 + c) : czero();
@@ -391,36 +396,49 @@ __device__ __forceinline__ void trtri_task(int N, const float4* A, const float2*
     ys[threadIdx.x] = df_make(v.x, v.y);
   }
   __syncthreads();
-  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
-  cacc acc[4];
-  cdf dv[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    acc[i] = cacc_zero();
-    dv[i] = czero();
-  }
-  for (int k = 0; k < NB; ++k) {
-    const df yk = ys[k];
-    const cdf lk = Ls[lane][k];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int j = warp + 8 * i;
-      if (k >= j) {
-        const cdf v = cdf_scale(cdf_sub(cdf_make(k == j ? one : zero, zero), cacc_val(acc[i])), yk);
-        const cdf b = shfl_cdf(v, k);
-        if (lane == k) dv[i] = b;
-        if (lane > k) cacc_mul(acc[i], lk, b);
-      }
+  // the 32 unit-vector solves (block b, column j) in two passes of 16 half-warps; rows above j
+  // come out as zero by themselves (right-hand side and accumulator are zero there)
+  const int hl = lane & (H - 1);
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int sp = 2 * warp + (lane >> 4) + H * pass;
+    const int b = sp / H, j = sp % H, o = b * H;
+    cacc acc = cacc_zero();
+    cdf dv = czero();
+    for (int k = 0; k < H; ++k) {
+      const cdf v = cdf_scale(cdf_sub(cdf_make(k == j ? one : zero, zero), cacc_val(acc)), ys[o + k]);
+      cdf bk;
+      bk.re.h = __shfl_sync(0xffffffffu, v.re.h, k, H);
+      bk.re.l = __shfl_sync(0xffffffffu, v.re.l, k, H);
+      bk.im.h = __shfl_sync(0xffffffffu, v.im.h, k, H);
+      bk.im.l = __shfl_sync(0xffffffffu, v.im.l, k, H);
+      if (hl == k) dv = bk;
+      if (hl > k) cacc_mul(acc, Ls[o + hl][o + k], bk);
     }
+    Ds[o + hl][o + j] = dv;
+    Ds[o + hl][H - o + j] = czero();      // the other 16 columns of these rows: D12 = 0 / D21 later
   }
-  if (r0 + lane < N) {
-    float4* Dr = D + ((size_t)jp * NB + lane) * NB;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) Dr[warp + 8 * i] = st4(dv[i]);
+  __syncthreads();
+  // T = L21 D11, then D21 = -D22 T
+  const int r = threadIdx.x / H, c = threadIdx.x % H;
+  cacc t = cacc_zero();
+#pragma unroll 4
+  for (int m = 0; m < H; ++m) cacc_mul(t, Ls[H + r][m], Ds[m][c]);
+  Ts[r][c] = cacc_val(t);
+  __syncthreads();
+  cacc u = cacc_zero();
+#pragma unroll 4
+  for (int m = 0; m < H; ++m) cacc_mul(u, Ds[H + r][H + m], Ts[m][c]);
+  const cdf d21 = cacc_val(u);
+  Ds[H + r][c] = cdf_make(df_neg(d21.re), df_neg(d21.im));
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
+    const int rr = e / NB, cc = e % NB;
+    if (r0 + rr < N) D[((size_t)jp * NB + rr) * NB + cc] = st4(Ds[rr][cc]);
   }
 }
 
-__global__ void __launch_bounds__(CS_THREADS) k_chol_step_df(int N, Batch mb, int nb, int li,
+__global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb, int nb, int li,
                                                             unsigned* ctl, int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ unsigned s_t;
