@@ -39,7 +39,8 @@ constexpr int ROWB = 128;      // bytes of one operand row per stage (one swizzl
 constexpr int STAGES = 2;
 constexpr int A_TILE = BM * ROWB;     // 16 KB
 constexpr int B_TILE = BNT * ROWB;    // 4 KB
-// stage layout: A_P_hi, A_P_lo, A_Q_hi, A_Q_lo, B_P_hi, B_P_lo, B_Q_hi, B_Q_lo
+// stage layout: A_P_hi, A_P_lo, A_Q_hi, A_Q_lo, B_P_hi, B_Q_hi, B_P_lo, B_Q_lo (the two hi and the
+// two lo ket tiles adjacent: each pair is one 64-row operand)
 constexpr int STAGE_BYTES = 4 * A_TILE + 4 * B_TILE;   // 80 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ket factors*/;
 constexpr int TMEM_COLS = 512;
@@ -125,10 +126,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 }
 
 // Instruction descriptor: D = F32, A = B = BF16 (kind 0) or TF32 (kind 1), both K-major,
-// M = 128, N = 32.
+// M = 128, N = 64 (the P and Q planes of 32 kets side by side).
+constexpr int BN_MMA = 2 * BNT;
 __host__ __device__ constexpr uint32_t idesc(int kind) {
-  return (1u << 4) | ((kind ? 2u : 1u) << 7) | ((kind ? 2u : 1u) << 10) | ((uint32_t)(BNT >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
+  return (1u << 4) | ((kind ? 2u : 1u) << 7) | ((kind ? 2u : 1u) << 10) |
+         ((uint32_t)(BN_MMA >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <int KIND>
@@ -268,8 +270,8 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
             // ket planes scaled by u_g: rows (2g) N + b and (2g+1) N + b
             unsigned char* sb = st + 4 * A_TILE;
             tma_load_2d(sb + 0 * B_TILE, mhb, kc, 2 * g * N + b0, full + slot);
-            tma_load_2d(sb + 1 * B_TILE, mlb, kc, 2 * g * N + b0, full + slot);
-            tma_load_2d(sb + 2 * B_TILE, mhb, kc, (2 * g + 1) * N + b0, full + slot);
+            tma_load_2d(sb + 1 * B_TILE, mhb, kc, (2 * g + 1) * N + b0, full + slot);
+            tma_load_2d(sb + 2 * B_TILE, mlb, kc, 2 * g * N + b0, full + slot);
             tma_load_2d(sb + 3 * B_TILE, mlb, kc, (2 * g + 1) * N + b0, full + slot);
           }
         }
@@ -295,25 +297,19 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
             fence_after();
             const uint32_t st = smem_u32(smem + slot * STAGE_BYTES);
             const uint32_t aph = st, apl = st + A_TILE, aqh = st + 2 * A_TILE, aql = st + 3 * A_TILE;
-            const uint32_t sb = st + 4 * A_TILE;
-            const uint32_t bph = sb, bpl = sb + B_TILE, bqh = sb + 2 * B_TILE, bql = sb + 3 * B_TILE;
+            const uint32_t bhi = st + 4 * A_TILE, blo = bhi + 2 * B_TILE;   // [P; Q] kets
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               const uint32_t o = kk * 32;   // 32 bytes of K per instruction
               const uint32_t first = (s == 0 && kk == 0) ? 0u : 1u;
-              // PP, PQ, QP, QQ, each hi*hi + hi*lo + lo*hi
-              mma<KIND>(acc + 0, sdesc(aph + o), sdesc(bph + o), first);
-              mma<KIND>(acc + 0, sdesc(aph + o), sdesc(bpl + o), 1u);
-              mma<KIND>(acc + 0, sdesc(apl + o), sdesc(bph + o), 1u);
-              mma<KIND>(acc + 32, sdesc(aph + o), sdesc(bqh + o), first);
-              mma<KIND>(acc + 32, sdesc(aph + o), sdesc(bql + o), 1u);
-              mma<KIND>(acc + 32, sdesc(apl + o), sdesc(bqh + o), 1u);
-              mma<KIND>(acc + 64, sdesc(aqh + o), sdesc(bph + o), first);
-              mma<KIND>(acc + 64, sdesc(aqh + o), sdesc(bpl + o), 1u);
-              mma<KIND>(acc + 64, sdesc(aql + o), sdesc(bph + o), 1u);
-              mma<KIND>(acc + 96, sdesc(aqh + o), sdesc(bqh + o), first);
-              mma<KIND>(acc + 96, sdesc(aqh + o), sdesc(bql + o), 1u);
-              mma<KIND>(acc + 96, sdesc(aql + o), sdesc(bqh + o), 1u);
+              // columns [0, 32) take the P kets, [32, 64) the Q kets: (PP, PQ) and (QP, QQ),
+              // each hi*hi + hi*lo + lo*hi
+              mma<KIND>(acc + 0, sdesc(aph + o), sdesc(bhi + o), first);
+              mma<KIND>(acc + 0, sdesc(aph + o), sdesc(blo + o), 1u);
+              mma<KIND>(acc + 0, sdesc(apl + o), sdesc(bhi + o), 1u);
+              mma<KIND>(acc + 64, sdesc(aqh + o), sdesc(bhi + o), first);
+              mma<KIND>(acc + 64, sdesc(aqh + o), sdesc(blo + o), 1u);
+              mma<KIND>(acc + 64, sdesc(aql + o), sdesc(bhi + o), 1u);
             }
             mma_commit(empty + slot);   // frees the stage when these MMAs complete
           }
