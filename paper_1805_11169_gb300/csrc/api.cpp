@@ -59,6 +59,8 @@ struct icwf_ctx {
   std::string err;
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;              // first RK4 stage, beside the assembly and factorisation
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool mixed = false;
   int N = 0, nx = 0, nR = 0, K = 0, logx = 0, logR = 0;
   double dx = 0, dR = 0;
@@ -156,20 +158,30 @@ cudaEvent_t take_event(icwf_ctx* h) {
   return e;
 }
 
+void destroy_streams(icwf_ctx* h) {
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  h->ev_fork = h->ev_join = nullptr;
+  h->side = h->stream = nullptr;
+}
+
 struct ProfScope {
   icwf_ctx* h;
   int fam;
+  cudaStream_t s;
   cudaEvent_t a = nullptr;
-  ProfScope(icwf_ctx* h_, int f) : h(h_), fam(f) {
+  ProfScope(icwf_ctx* h_, int f, cudaStream_t s_ = nullptr) : h(h_), fam(f), s(s_ ? s_ : h_->stream) {
     if (h->prof_on) {
       a = take_event(h);
-      cudaEventRecord(a, h->stream);
+      cudaEventRecord(a, s);
     }
   }
   ~ProfScope() {
     if (h->prof_on) {
       cudaEvent_t b = take_event(h);
-      cudaEventRecord(b, h->stream);
+      cudaEventRecord(b, s);
       h->pending.push_back({fam, {a, b}});
     }
   }
@@ -293,15 +305,16 @@ void factor(icwf_ctx* h, int n, const double2* const* S0, const double2* const* 
 }
 
 void solve(icwf_ctx* h, const double2* Lf, const double2* D, const double2* y, double2* out,
-           bool minus_i) {
-  ProfScope ps(h, F_SOLVE);
+           bool minus_i, cudaStream_t s = nullptr) {
+  if (!s) s = h->stream;
+  ProfScope ps(h, F_SOLVE, s);
   ++h->epoch;
   if (h->mixed)
     launch_chol_solve_df(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
-                         h->status, h->stream);
+                         h->status, s);
   else
     launch_chol_solve(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
-                      h->status, h->stream);
+                      h->status, s);
   h->launches += 2;
 }
 
@@ -317,10 +330,32 @@ void assemble(icwf_ctx* h, double2* S, double2* Hm) {
 }
 
 // One ICWF step t_n -> t_{n+1}.
+// The RK4 stages that need only data of t_n (the first stage; all four with frozen matrices) run on
+// a side stream from the start of the step, beside the velocities, propagation, assembly and
+// factorisation, which do not touch their inputs or outputs; the main stream joins them before
+// the later stages (they share the right-hand-side buffer and the solve scratch).
 void step_once(icwf_ctx* h) {
   JobView j = view(h);
   const int cur = h->cur, nxt = 1 - cur;
   const double dt = h->p.dt;
+  double2 *Lc = h->L[cur], *Ln = h->L[nxt];
+  double *in = h->invL[nxt];
+  double2 *Dc = h->DL[cur], *Dn = h->DL[nxt];
+  const bool frozen = h->p.coeff_scheme == 1;
+  cudaEventRecord(h->ev_fork, h->stream);
+  cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+  for (int st = 0; st < (frozen ? 4 : 1); ++st) {
+    // S, Heff at t_n (frozen over the step) or the first stage of the interpolated scheme
+    const double c = st == 0 ? 0.0 : (st == 3 ? dt : 0.5 * dt);
+    {
+      ProfScope ps(h, F_MATVEC, h->side);
+      launch_matvec(h->N, h->H[cur], h->H[cur], 0.0, h->C, st ? h->kk[st - 1] : nullptr, c, h->y,
+                    h->side);
+      h->launches += 1;
+    }
+    solve(h, Lc, Dc, h->y, h->kk[st], true, h->side);
+  }
+  cudaEventRecord(h->ev_join, h->side);
   {
     ProfScope ps(h, F_VELOCITY);
     if (h->mixed) launch_velocity<float>(j, h->C, h->stream);
@@ -334,27 +369,14 @@ void step_once(icwf_ctx* h) {
     h->launches += 1;
   }
   assemble(h, h->S[nxt], h->H[nxt]);
-  double2 *Lc = h->L[cur], *Ln = h->L[nxt];
-  double *ic = h->invL[cur], *in = h->invL[nxt];
-  double2 *Dc = h->DL[cur], *Dn = h->DL[nxt];
-  if (h->p.coeff_scheme == 1) {
-    // S, Heff frozen at t_n over the step: every stage uses L[cur], H[cur]
-    for (int st = 0; st < 4; ++st) {
-      const double c = st == 0 ? 0.0 : (st == 3 ? dt : 0.5 * dt);
-      {
-        ProfScope ps(h, F_MATVEC);
-        launch_matvec(h->N, h->H[cur], h->H[cur], 0.0, h->C, st ? h->kk[st - 1] : nullptr, c, h->y,
-                      h->stream);
-        h->launches += 1;
-      }
-      solve(h, Lc, Dc, h->y, h->kk[st], true);
-    }
+  if (frozen) {
     const double2* s0[1] = {h->S[nxt]};
     const double th[1] = {1.0};
     double2* d[1] = {Ln};
     double* iv[1] = {in};
     double2* dd[1] = {Dn};
     factor(h, 1, s0, s0, th, d, iv, dd);
+    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   } else {
     const double2* s0[2] = {h->S[cur], h->S[nxt]};
     const double2* s1[2] = {h->S[nxt], h->S[nxt]};
@@ -363,15 +385,16 @@ void step_once(icwf_ctx* h) {
     double* iv[2] = {h->invLh, in};
     double2* dd[2] = {h->DLh, Dn};
     factor(h, 2, s0, s1, th, d, iv, dd);
+    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
     const double thetas[4] = {0.0, 0.5, 0.5, 1.0};
     const double2* Ls[4] = {Lc, h->Lh, h->Lh, Ln};
     const double2* Is[4] = {Dc, h->DLh, h->DLh, Dn};
-    for (int st = 0; st < 4; ++st) {
-      const double c = st == 0 ? 0.0 : (st == 3 ? dt : 0.5 * dt);
+    for (int st = 1; st < 4; ++st) {
+      const double c = st == 3 ? dt : 0.5 * dt;
       {
         ProfScope ps(h, F_MATVEC);
-        launch_matvec(h->N, h->H[cur], h->H[nxt], thetas[st], h->C, st ? h->kk[st - 1] : nullptr,
-                      c, h->y, h->stream);
+        launch_matvec(h->N, h->H[cur], h->H[nxt], thetas[st], h->C, h->kk[st - 1], c, h->y,
+                      h->stream);
         h->launches += 1;
       }
       solve(h, Ls[st], Is[st], h->y, h->kk[st], true);
@@ -536,8 +559,13 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   }
 
   // ---- device memory ----
-  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    destroy_streams(h);
     return fail(nullptr, ICWF_ERR_CUDA, "icwf_create: cudaStreamCreate failed");
+  }
   const int N = h->N;
   const size_t cw = h->cwf_elem, rw = h->mixed ? sizeof(float) : sizeof(double);
   const size_t NN = (size_t)N * N;
@@ -563,7 +591,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   }
   total += 4096;
   if (cudaMalloc(&h->arena.base, total) != cudaSuccess) {
-    cudaStreamDestroy(h->stream);
+    destroy_streams(h);
     return fail(nullptr, ICWF_ERR_OOM, "icwf_create: cudaMalloc of " + std::to_string(total) + " bytes failed");
   }
   h->arena.size = total;
@@ -614,7 +642,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   if (h->mixed) h->tc_scratch = a.take(h->tc_scratch_bytes);
   if (!h->status || (h->mixed && !h->tc_scratch)) {
     cudaFree(h->arena.base);
-    cudaStreamDestroy(h->stream);
+    destroy_streams(h);
     return fail(nullptr, ICWF_ERR_OOM, "icwf_create: arena layout overflow");
   }
 
@@ -623,7 +651,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   kinetic_tables(nx, h->dx, p.mass_x, p.dt, kx, twx);
   kinetic_tables(nR, h->dR, p.mass_R, p.dt, kR, twR);
   icwf_status st;
-#define UP(dst, src, bytes) do { st = upload(h, dst, src, bytes); if (st) { g_err = h->err; cudaFree(h->arena.base); cudaStreamDestroy(h->stream); return st; } } while (0)
+#define UP(dst, src, bytes) do { st = upload(h, dst, src, bytes); if (st) { g_err = h->err; cudaFree(h->arena.base); destroy_streams(h); return st; } } while (0)
   UP(h->V, Vh, nV * 8);
   std::vector<float> Vf, kxf, kRf, twxf, twRf;
   if (h->mixed) {
@@ -654,7 +682,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
       cudaMemsetAsync(h->status, 0, 64 * 4, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaFree(h->arena.base);
-    cudaStreamDestroy(h->stream);
+    destroy_streams(h);
     return fail(nullptr, ICWF_ERR_CUDA, "icwf_create: initial device transfer failed");
   }
   *out = hp.release();
@@ -672,7 +700,7 @@ icwf_status icwf_destroy(icwf_handle h) {
   for (void* p : h->extra_allocs) cudaFree(p);
   if (h->phi) cudaFree(h->phi);
   if (h->arena.base) cudaFree(h->arena.base);
-  if (h->stream) cudaStreamDestroy(h->stream);
+  destroy_streams(h);
   delete h;
   return ICWF_OK;
 }
