@@ -320,7 +320,7 @@ void solve(icwf_ctx* h, const double2* Lf, const double2* D, const double2* y, d
 
 void assemble(icwf_ctx* h, double2* S, double2* Hm) {
   ProfScope ps(h, F_ASSEMBLE);
-  h->launches += 1;
+  h->launches += h->mixed ? 3 : 1;   // operand planes (two sides) + Grams, or the FP64 kernel
   JobView j = view(h);
   if (h->mixed) {
     launch_assemble_tc(j, h->p.precision, S, Hm, h->tc_scratch, h->tc_scratch_bytes, h->stream);
