@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="tf32x3", choices=list(MODES))
+    ap.add_argument("--solve", default="df64", choices=["df64", "fp64"],
+                    help="mixed modes: Cholesky and triangular solves in double-float (default) "
+                         "or FP64")
     ap.add_argument("--n-traj", type=int, default=1024)
     ap.add_argument("--nx", type=int, default=1024, help="electron grid points (profiling cases)")
     ap.add_argument("--nR", type=int, default=512, help="nuclear grid points (profiling cases)")
@@ -177,7 +180,7 @@ def algorithmic_work(fam, w, K, mode):
     return None
 
 
-def roofline(prof, w, K, mode, peaks):
+def roofline(prof, w, K, mode, peaks, solve="df64"):
     fam = max(prof, key=lambda f: prof[f][0])
     ms, n = prof[fam]
     work = algorithmic_work(fam, w, K, mode)
@@ -192,7 +195,7 @@ def roofline(prof, w, K, mode, peaks):
     elif bound == "tensor":
         out.update(bound="tensor", achieved=rate / 1e12, peak=peaks.get("bf16_tflops_sustained"),
                    unit="TFLOP/s", peak_source="measured bf16 sustained (MEASURED_PEAKS.json)")
-    elif mode == "fp64":
+    elif mode == "fp64" or solve == "fp64":
         out.update(bound="alu", achieved=rate / 1e12, peak=NOMINAL_FP64_TFLOPS, unit="TFLOP/s",
                    peak_source="nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)")
     else:
@@ -215,7 +218,7 @@ def run_ours(args, rank, ws, local):
     torch.cuda.set_device(local)
     prec, dtype_name, cutoff, eps = MODES[args.mode]
     w = make_workload(args.n_traj, cutoff, eps, args.nx, args.nR)
-    params = g.params_from(w, precision=prec)
+    params = g.params_from(w, precision=prec, solve_fp64=int(args.solve == "fp64"))
 
     sim = g.Icwf(params, w.V)
     sim.set_projectors(w.phi)
@@ -261,7 +264,7 @@ def run_ours(args, rank, ws, local):
     except (OSError, ValueError):
         peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
     prof_step = {f: v for f, v in prof.items() if v[1] > 0 and f != "observables"}
-    rl = roofline(prof_step, w, info["rank"], args.mode, peaks)
+    rl = roofline(prof_step, w, info["rank"], args.mode, peaks, args.solve)
 
     out = {
         "metric": "ICWF trajectory-steps/s at N=1024",
@@ -279,6 +282,8 @@ def run_ours(args, rank, ws, local):
         "config": {"workload": workload_name(w), "nx": w.nx, "nR": w.nR, "n_traj": w.n_traj,
                    "dt": w.dt, "rank_k": info["rank"], "svd_rel_cutoff": cutoff, "s_reg_eps": eps,
                    "svd_tail_rel": info["tail_rel"], "coeff_scheme": "rk4-interpolated",
+                   "solve": ("fp64" if args.mode == "fp64" or args.solve == "fp64"
+                             else "double-float (FP32 pairs)"),
                    "obs_every": OBS_EVERY, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": rl,

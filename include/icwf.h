@@ -54,7 +54,10 @@ typedef enum {
   ICWF_FP64 = 0,          /* CWFs complex128; matrix elements, solve and RK4 in FP64 */
   ICWF_MIXED_BF16X3 = 1,  /* CWFs complex64, FP32 propagation; Grams on tcgen05 tensor cores as
                              three BF16 products (hi*hi + hi*lo + lo*hi), FP32 accumulation;
-                             S regularisation, Cholesky, RK4 and reductions in FP64 */
+                             S and Heff stored in FP64; S + eps*I formed in FP64; Cholesky and
+                             triangular solves in double-float arithmetic (pairs of FP32, about
+                             44-48 significant bits) unless solve_fp64 is set; right-hand sides,
+                             RK4 update and reductions in FP64 */
   ICWF_MIXED_TF32X3 = 2   /* as above with TF32 operand pieces */
 } icwf_precision;
 
@@ -71,6 +74,9 @@ typedef struct {
   int32_t coeff_scheme;     /* 0: RK4 with S, Heff linear in t over the step (two Cholesky
                                factorisations per step); 1: S, Heff frozen at t_n (one) */
   int32_t max_rank;         /* upper bound on the kept rank k (0: no bound beyond the cutoff) */
+  int32_t solve_fp64;       /* mixed modes only: 1 runs the Cholesky factorisations and triangular
+                               solves in FP64 (as ICWF_FP64 does) instead of double-float;
+                               ignored by ICWF_FP64 */
 } icwf_params;
 
 /* Diagnostic facts about a handle. */

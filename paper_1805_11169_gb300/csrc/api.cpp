@@ -62,6 +62,7 @@ struct icwf_ctx {
   cudaStream_t side = nullptr;              // first RK4 stage, beside the assembly and factorisation
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool mixed = false;
+  bool df_solve = false;                    // factorisation and solves in double-float arithmetic
   int N = 0, nx = 0, nR = 0, K = 0, logx = 0, logR = 0;
   double dx = 0, dR = 0;
   double tail_rel = 0, next_rel = 0, sigma_max = 0;
@@ -288,13 +289,13 @@ void factor(icwf_ctx* h, int n, const double2* const* S0, const double2* const* 
   {
     ProfScope ps(h, F_SHIFT);
     for (int m = 0; m < n; ++m) {
-      if (h->mixed) launch_shift_mix_df(h->N, S0[m], S1[m], h->p.s_reg_eps, theta[m], dst[m], h->stream);
+      if (h->df_solve) launch_shift_mix_df(h->N, S0[m], S1[m], h->p.s_reg_eps, theta[m], dst[m], h->stream);
       else launch_shift_mix(h->N, S0[m], S1[m], h->p.s_reg_eps, theta[m], dst[m], h->stream);
     }
     h->launches += n;
   }
   ProfScope ps(h, F_POTRF);
-  if (h->mixed) {
+  if (h->df_solve) {
     void* a[2] = {dst[0], n > 1 ? dst[1] : dst[0]};
     void* iv[2] = {inv[0], n > 1 ? inv[1] : inv[0]};
     void* dd[2] = {D[0], n > 1 ? D[1] : D[0]};
@@ -309,7 +310,7 @@ void solve(icwf_ctx* h, const double2* Lf, const double2* D, const double2* y, d
   if (!s) s = h->stream;
   ProfScope ps(h, F_SOLVE, s);
   ++h->epoch;
-  if (h->mixed)
+  if (h->df_solve)
     launch_chol_solve_df(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
                          h->status, s);
   else
@@ -498,6 +499,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   h->dx = (p.x_max - p.x_min) / p.nx;
   h->dR = (p.R_max - p.R_min) / p.nR;
   h->mixed = p.precision != ICWF_FP64;
+  h->df_solve = h->mixed && !p.solve_fp64;
   h->cwf_elem = h->mixed ? sizeof(float2) : sizeof(double2);
   cudaGetDevice(&h->device);
 
