@@ -37,6 +37,10 @@ NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 (vector and DMMA alike), nominal
 FP32_LANE_OPS = 152 * 128 * 2.07e9
 DF64_CMAC_OPS = 39
 DF64_TFLOPS = FP32_LANE_OPS * 8 / DF64_CMAC_OPS / 1e12
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
+# DRAM bytes (read + write) per family call from one ncu capture, with the profile that gives them;
+# keyed by (family, mode, N).  Valid only while the kernels are the ones profiled.
+TRAFFIC = {("cholesky", "tf32x3", 1024): (193.3e6, "profiles/k_chol_step_df_mixed_N1024.md")}
 
 
 def parse():
@@ -193,8 +197,14 @@ def roofline(prof, w, K, mode, peaks, solve="df64"):
         out.update(bound="hbm", achieved=rate / 1e9, peak=peaks.get("hbm_gbs"), unit="GB/s",
                    peak_source="measured (MEASURED_PEAKS.json hbm_gbs)")
     elif bound == "tensor":
-        out.update(bound="tensor", achieved=rate / 1e12, peak=peaks.get("bf16_tflops_sustained"),
-                   unit="TFLOP/s", peak_source="measured bf16 sustained (MEASURED_PEAKS.json)")
+        # algorithmic Gram flops against the split-product ceiling: three products per Gram in the
+        # operand type (TF32 at the nominal TF32/BF16 ratio of the measured BF16 peak)
+        bf16 = peaks.get("bf16_tflops_sustained")
+        ratio = TF32_PER_BF16 if mode == "tf32x3" else 1.0
+        out.update(bound="tensor", achieved=rate / 1e12,
+                   peak=bf16 * ratio / 3 if bf16 else None, unit="TFLOP/s",
+                   peak_source=("measured bf16 sustained (MEASURED_PEAKS.json) x %.3f (nominal "
+                                "%s/BF16) / 3 split products" % (ratio, "TF32" if ratio < 1 else "BF16")))
     elif mode == "fp64" or solve == "fp64":
         out.update(bound="alu", achieved=rate / 1e12, peak=NOMINAL_FP64_TFLOPS, unit="TFLOP/s",
                    peak_source="nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)")
@@ -204,7 +214,11 @@ def roofline(prof, w, K, mode, peaks, solve="df64"):
                                "8 flops per 39 FP32 operations (FP64-equivalent flops)")
     if out.get("peak"):
         out["frac"] = out["achieved"] / out["peak"]
-    out["traffic"] = None
+    tr = TRAFFIC.get((fam, mode if solve == "df64" else "fp64-solve", w.n_traj))
+    out["traffic"] = tr[0] if tr else None
+    if tr:
+        out["traffic_unit"] = "bytes per call (DRAM read + write, ncu)"
+        out["traffic_source"] = tr[1]
     return out
 
 
