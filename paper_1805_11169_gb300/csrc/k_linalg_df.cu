@@ -193,6 +193,7 @@ __device__ __forceinline__ cdf upd_one(const float4* A, int N, int xrow0, int yr
                                        int orow, int ocol, bool ok, unsigned char* smem) {
   df(*Xp)[R][NB] = (df(*)[R][NB])smem;                        // [3][R][32]
   df(*Yp)[NB][C] = (df(*)[NB][C])(smem + 3 * R * NB * 8);     // [3][32][C]
+  const cdf a = ok ? ldcg4(A + (size_t)orow * N + ocol) : czero();   // issued first, used last
   for (int e = threadIdx.x; e < R * NB; e += CS_THREADS) {
     const int r = e / NB, k = e % NB;
     cdf x = czero();
@@ -218,7 +219,6 @@ __device__ __forceinline__ cdf upd_one(const float4* A, int N, int xrow0, int yr
     acc_prod_df(p2, Xp[1][r][k], Yp[1][k][c]);
     acc_prod_df(p3, Xp[2][r][k], Yp[2][k][c]);
   }
-  const cdf a = ok ? ldcg4(A + (size_t)orow * N + ocol) : czero();
   __syncthreads();
   return cdf_sub(a, kara_val(p1, p2, p3));
 }
@@ -517,26 +517,38 @@ __global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb,
       __threadfence();
     }
     __syncthreads();
+    // with L' = L diag(y) (y_k = 1 / L_kk) and x = z diag(y): z_k = a_k - sum_j<k z_j conj(L'_kj),
+    // so the chain carries no scaling; L' is formed while staging the block
     cdf(*Ls)[NB + 1] = (cdf(*)[NB + 1])sm;                      // [32][33]
     df* ys = (df*)(sm + NB * (NB + 1) * 16);
-    for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
-      const int rr = e / NB, cc = e % NB;
-      Ls[rr][cc] = cc < rr ? ldcg4(A + (size_t)(jp * NB + rr) * N + jp * NB + cc) : czero();
-    }
     if (threadIdx.x < NB) {
       const float2 v = __ldcg(inv + jp * NB + threadIdx.x);
       ys[threadIdx.x] = df_make(v.x, v.y);
     }
     __syncthreads();
-    cacc s = cacc_zero();
-    cdf x = czero();
-    for (int k = 0; k < NB; ++k) {
-      const cdf v = cdf_scale(cdf_sub_sloppy(a, cacc_val(s)), ys[k]);
-      const cdf xk = shfl_cdf(v, k);
-      if (c == k) x = xk;
-      if (c > k) cacc_mulc(s, xk, Ls[c][k]);
+    for (int e = threadIdx.x; e < NB * NB; e += CS_THREADS) {
+      const int rr = e / NB, cc = e % NB;
+      Ls[rr][cc] = cc < rr ? cdf_scale(ldcg4(A + (size_t)(jp * NB + rr) * N + jp * NB + cc), ys[cc])
+                           : czero();
     }
-    if (ok) A[(size_t)(i0 + r) * N + jp * NB + c] = st4(x);
+    __syncthreads();
+    cacc s = cacc_zero();
+    cdf z = czero();
+    cdf lnext = Ls[c][0];
+#pragma unroll 4
+    for (int k = 0; k < NB; ++k) {
+      const cdf lk = lnext;
+      if (k + 1 < NB) lnext = Ls[c][k + 1];   // next step's operand, off the chain
+      const cdf zk = shfl_cdf(cdf_sub_sloppy(a, cacc_val(s)), k);
+      if (c == k) z = zk;
+      if (c > k) cacc_mulc(s, zk, lk);
+    }
+    if (ok) {
+      const cdf x = cdf_scale(z, ys[c]);
+      A[(size_t)(i0 + r) * N + jp * NB + c] = st4(x);
+      // L^H in the (otherwise unused) upper triangle: the backward solve reads it by rows
+      A[(size_t)(jp * NB + c) * N + i0 + r] = st4(cdf_make(x.re, df_neg(x.im)));
+    }
   }
 }
 
@@ -732,13 +744,14 @@ __global__ void __launch_bounds__(TW * 32) k_trsv_upper_df(int N, const float4* 
 
 // Both triangular solves of one RK4 stage in a single launch of one 8-CTA thread-block cluster.
 // Every CTA keeps the whole forward solution z and backward solution w in its shared memory.
-// CTA rank r owns block rows jb = r, r + 8, ...; when it finishes a block it pushes the 32 values
-// to all eight CTAs with bulk shared-to-shared copies (DSMEM) that complete the transaction count
-// of the receiver's per-block mbarrier, so consumers wait on a local barrier instead of polling
+// CTA rank r owns block rows jb = r, r + 8, ...; when it finishes a block, the 32 values go from
+// registers into all eight CTAs' shared memory by st.async, completing the transaction count of
+// the receiver's per-block mbarrier, so consumers wait on a local barrier instead of polling
 // global memory.  The loops are block-major: on the arrival of block m every CTA adds that block's
 // products to all of its pending rows, and finishes its own row m + 1 (forward) / m - 1 (backward)
 // as soon as the block it depends on is in.  Products use compensated double-float dot products;
-// the critical block's columns are split over the eight warps and merged through shared memory.
+// a block is spread as 8 warps x 4 rows, 8 lanes per row with 4 columns each, so the sums over a
+// row are 3 shuffle steps and the critical path has a single CTA barrier per block.
 constexpr int CL = 8;          // CTAs per cluster
 constexpr int CRPC = 8;        // maximum block rows per CTA (N <= CL * CRPC * 32 = 2048)
 constexpr int CTH = 256;       // threads per CTA
@@ -792,20 +805,16 @@ __device__ __forceinline__ bool block_wait(uint64_t* b, volatile int* abort_flag
   }
   return true;
 }
-// push 512 bytes of a finished block from local staging to every CTA of the cluster
-__device__ __forceinline__ void push_block(const float4* stage, float4* dst_local, uint64_t* bar_local) {
-  const uint32_t src = s_u32(stage);
-#pragma unroll
-  for (uint32_t r = 0; r < CL; ++r) {
-    const uint32_t dst = map_rank(s_u32(dst_local), r);
-    const uint32_t bar = map_rank(s_u32(bar_local), r);
-    asm volatile(
-        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(dst), "r"(src), "r"(512u), "r"(bar)
-        : "memory");
-  }
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+// store 16 bytes into CTA `rank`'s shared memory (the address is this CTA's twin of it) and
+// complete 16 bytes of the transaction count of that CTA's barrier `bar`
+__device__ __forceinline__ void st_async16(float4 v, const void* dst_local, uint64_t* bar_local,
+                                           uint32_t rank) {
+  const uint32_t dst = map_rank(s_u32(dst_local), rank);
+  const uint32_t bar = map_rank(s_u32(bar_local), rank);
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+      ::"r"(dst), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+      : "memory");
 }
 
 // Shared-memory layout of the cluster solve (per CTA).
@@ -813,74 +822,81 @@ struct CLayout {
   float4* zs;        // nblk*32 forward solution
   float4* ws;        // nblk*32 backward solution
   float4* yown;      // CRPC*32 right-hand side of the own rows (double-floats)
-  float4* stage;     // 32 outgoing block
-  cacc* part;        // 8*32 cross-warp partial sums
-  cdf* vsh;          // 32
+  cdf* vsh;          // 32: right-hand side minus products, for the diagonal-block product
   uint64_t* barF;    // nblk
   uint64_t* barB;    // nblk
   int* abort_flag;
 };
 __host__ __device__ inline size_t clayout_bytes(int nblk) {
-  return (size_t)(2 * nblk + CRPC + 1) * NB * 16 + (size_t)8 * NB * 16 + NB * 16 + (size_t)2 * nblk * 8 + 16;
+  return (size_t)(2 * nblk + CRPC + 1) * NB * 16 + (size_t)2 * nblk * 8 + 16;
 }
 __device__ __forceinline__ CLayout clayout(unsigned char* base, int nblk) {
   CLayout c;
   c.zs = (float4*)base;
   c.ws = c.zs + nblk * NB;
   c.yown = c.ws + nblk * NB;
-  c.stage = c.yown + CRPC * NB;
-  c.part = (cacc*)(c.stage + NB);
-  c.vsh = (cdf*)(c.part + 8 * NB);
+  c.vsh = (cdf*)(c.yown + CRPC * NB);
   c.barF = (uint64_t*)(c.vsh + NB);
   c.barB = c.barF + nblk;
   c.abort_flag = (int*)(c.barB + nblk);
   return c;
 }
 
-// Finish block row m.  `mine` holds this warp's share of the products with all other blocks; the
-// eight shares are merged, subtracted from the right-hand side, multiplied by the inverted diagonal
-// block (D_m forward, D_m^H backward; `dk` are this warp's four columns of it, prefetched), and the
-// 32 values are pushed to every CTA of the cluster.  Backward blocks are also written to `out`.
+// Sum over the 8 lanes of a row group (lane bits 0..2): every lane gets the same value, since the
+// compensated merge is symmetric in its operands.
+__device__ __forceinline__ cacc group_sum(cacc a) {
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    cacc b;
+    b.re.s = __shfl_xor_sync(0xffffffffu, a.re.s, o);
+    b.re.c = __shfl_xor_sync(0xffffffffu, a.re.c, o);
+    b.im.s = __shfl_xor_sync(0xffffffffu, a.im.s, o);
+    b.im.c = __shfl_xor_sync(0xffffffffu, a.im.c, o);
+    a = cacc_merge(a, b);
+  }
+  return a;
+}
+
+// Finish block row m: `mine` is this lane's share (its 4 columns) of the products with all other
+// blocks.  The 8 shares of a row are summed by shuffles, subtracted from the right-hand side,
+// multiplied by the inverted diagonal block (D_m forward, D_m^H backward; `dk` are this lane's 4
+// entries of it, prefetched) and summed again; lane 0 of each row group then stores the value
+// straight into all eight CTAs (st.async, completing on their barriers for block m).
 template <bool FWD>
 __device__ __forceinline__ void finish_block(const CLayout& c, int N, int m, const cacc& mine,
                                              const cdf (&dk)[4], double2* out, bool minus_i) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c0w = warp * 4;
-  const int row = m * NB + lane;
-  c.part[warp * NB + lane] = mine;
-  __syncthreads();
-  if (warp == 0) {
-    cacc s = c.part[lane];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) s = cacc_merge(s, c.part[w * NB + lane]);
-    const cdf rhs = FWD ? ld4(c.yown[(m / CL) * NB + lane]) : ld4(c.zs[row < N ? row : 0]);
-    c.vsh[lane] = row < N ? cdf_sub(rhs, cacc_val(s)) : czero();
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rb = warp * 4 + (lane >> 3), c0 = (lane & 7) * 4;
+  const int row = m * NB + rb;
+  const cdf s = cacc_val(group_sum(mine));
+  const cdf rhs = FWD ? ld4(c.yown[(m / CL) * NB + rb]) : ld4(c.zs[row < N ? row : 0]);
+  if ((lane & 7) == 0) c.vsh[rb] = row < N ? cdf_sub(rhs, s) : czero();
   __syncthreads();
   cacc o = cacc_zero();
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (FWD) cacc_mul(o, dk[q], c.vsh[c0w + q]);
-    else cacc_cmul(o, dk[q], c.vsh[c0w + q]);
+    if (FWD) cacc_mul(o, dk[q], c.vsh[c0 + q]);
+    else cacc_cmul(o, dk[q], c.vsh[c0 + q]);
   }
-  c.part[warp * NB + lane] = o;
-  __syncthreads();
-  if (warp == 0) {
-    cacc s = c.part[lane];
+  const cdf v = cacc_val(group_sum(o));
+  if ((lane & 7) == 0) {
+    const cdf vv = row < N ? v : czero();
+    const float4 f = st4(vv);
+    float4* dst = (FWD ? c.zs : c.ws) + row;
+    uint64_t* bar = (FWD ? c.barF : c.barB) + m;
+    if (!*(volatile int*)c.abort_flag) {
 #pragma unroll
-    for (int w = 1; w < 8; ++w) s = cacc_merge(s, c.part[w * NB + lane]);
-    const cdf v = row < N ? cacc_val(s) : czero();
-    c.stage[lane] = st4(v);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncwarp();
-    if (lane == 0 && !*(volatile int*)c.abort_flag)
-      push_block(c.stage, (FWD ? c.zs : c.ws) + m * NB, (FWD ? c.barF : c.barB) + m);
-    __syncwarp();
+      for (uint32_t r = 0; r < CL; ++r) st_async16(f, dst, bar, r);
+    }
     if (!FWD && row < N) {
-      const double re = df_to(v.re), im = df_to(v.im);
+      const double re = df_to(vv.re), im = df_to(vv.im);
       out[row] = minus_i ? make_double2(im, -re) : make_double2(re, im);
     }
   }
-  __syncthreads();
+}
+
+__device__ __forceinline__ void pf_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 // Waits for block m on a local barrier; the outcome is made uniform over the CTA.
@@ -898,7 +914,8 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
   const CLayout c = clayout(csm, nblk);
   const int rank = (int)cluster_rank();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0w = warp * 4;                        // this warp's 4 columns of a block
+  const int rb = warp * 4 + (lane >> 3);     // this lane's row within a block
+  const int c0 = (lane & 7) * 4;             // and its 4 columns
 
   if (threadIdx.x == 0) {
     for (int m = 0; m < nblk; ++m) {
@@ -929,7 +946,7 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
   bool alive = true;
   if (rank == 0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dk[q] = lane < N ? ld4(D[(size_t)lane * NB + c0w + q]) : czero();
+    for (int q = 0; q < 4; ++q) dk[q] = rb < N ? ld4(D[(size_t)rb * NB + c0 + q]) : czero();
     finish_block<true>(c, N, 0, cacc_zero(), dk, out, minus_i);
   }
   for (int m = 0; m < nblk; ++m) {
@@ -937,17 +954,17 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
     const bool crit = mc < nblk && mc % CL == rank;
     if (crit) {
       // prefetch the critical row's operands before the wait: L[mc, m] and D_mc
-      const int row = mc * NB + lane;
+      const int row = mc * NB + rb;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        lk[q] = row < N ? ld4(__ldg(L + (size_t)row * N + m * NB + c0w + q)) : czero();
-        dk[q] = row < N ? ld4(__ldg(D + (size_t)row * NB + c0w + q)) : czero();
+        lk[q] = row < N ? ld4(__ldg(L + (size_t)row * N + m * NB + c0 + q)) : czero();
+        dk[q] = row < N ? ld4(__ldg(D + (size_t)row * NB + c0 + q)) : czero();
       }
     }
     if (!cta_wait_block(c, c.barF + m, status)) { alive = false; break; }
     cdf zc[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) zc[q] = ld4(c.zs[m * NB + c0w + q]);
+    for (int q = 0; q < 4; ++q) zc[q] = ld4(c.zs[m * NB + c0 + q]);
     if (crit) {
       cacc mine = cacc_zero();
 #pragma unroll
@@ -960,11 +977,22 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
 #pragma unroll
     for (int i = 0; i < CRPC; ++i) {
       const int jb = rank + CL * i;
-      const int row = jb * NB + lane;
+      const int row = jb * NB + rb;
       if (jb > mc && jb < nblk && row < N) {
-        const float4* lp = L + (size_t)row * N + m * NB + c0w;
+        const float4* lp = L + (size_t)row * N + m * NB + c0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) cacc_mul(acc[i], ld4(__ldg(lp + q)), zc[q]);
+        // the next block's operands of this row, into L1 while the CTA waits for that block
+        if (jb > mc + 1) pf_l1(lp + NB);
+      }
+    }
+    // operands of this CTA's next critical step (block m + 2 at the next arrival) into L1 now:
+    // that step starts right after its block arrives, too soon to wait for L2
+    if (m + 2 < nblk && (m + 2) % CL == rank) {
+      const int row = (m + 2) * NB + rb;
+      if (row < N) {
+        pf_l1(L + (size_t)row * N + (m + 1) * NB + c0);
+        pf_l1(D + (size_t)row * NB + c0);
       }
     }
   }
@@ -976,8 +1004,8 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
     if (last % CL == rank) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int r = last * NB + c0w + q;
-        dk[q] = r < N ? ld4(D[(size_t)r * NB + lane]) : czero();
+        const int r = last * NB + c0 + q;
+        dk[q] = r < N ? ld4(D[(size_t)r * NB + rb]) : czero();
       }
       finish_block<false>(c, N, last, cacc_zero(), dk, out, minus_i);
     }
@@ -985,45 +1013,55 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
       const int mc = m - 1;
       const bool crit = mc >= 0 && mc % CL == rank;
       if (crit) {
-        // L[m, mc]^H and D_mc^H: this warp's four rows of block m / of D_mc, column `lane`
+        // (L^H)[mc, m] from the upper triangle (row mc*32 + rb, columns c0.. of block m) and D_mc^H
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int rm = m * NB + c0w + q;
-          lk[q] = rm < N ? ld4(__ldg(L + (size_t)rm * N + mc * NB + lane)) : czero();
-          dk[q] = ld4(__ldg(D + (size_t)(mc * NB + c0w + q) * NB + lane));
+          const int rm = m * NB + c0 + q;
+          lk[q] = rm < N ? ld4(__ldg(L + (size_t)(mc * NB + rb) * N + rm)) : czero();
+          dk[q] = ld4(__ldg(D + (size_t)(mc * NB + c0 + q) * NB + rb));
         }
       }
       if (!cta_wait_block(c, c.barB + m, status)) break;
       cdf wc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) wc[q] = ld4(c.ws[m * NB + c0w + q]);
+      for (int q = 0; q < 4; ++q) wc[q] = ld4(c.ws[m * NB + c0 + q]);
       if (crit) {
         cacc mine = cacc_zero();
 #pragma unroll
         for (int i = 0; i < CRPC; ++i) if (rank + CL * i == mc) mine = acc[i];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cacc_cmul(mine, lk[q], wc[q]);
+        for (int q = 0; q < 4; ++q) cacc_mul(mine, lk[q], wc[q]);
         finish_block<false>(c, N, mc, mine, dk, out, minus_i);
       }
-      // the remaining own rows jb < m - 1: acc += L[m, jb]^H w_m
+      // the remaining own rows jb < m - 1: acc += (L^H)[jb, m] w_m, read by rows of the upper triangle
 #pragma unroll
       for (int i = 0; i < CRPC; ++i) {
         const int jb = rank + CL * i;
         if (jb < mc) {
-          const int col = jb * NB + lane;
+          const float4* up = L + (size_t)(jb * NB + rb) * N + m * NB + c0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int rm = m * NB + c0w + q;
-            if (rm < N) cacc_cmul(acc[i], ld4(__ldg(L + (size_t)rm * N + col)), wc[q]);
-          }
+          for (int q = 0; q < 4; ++q)
+            if (m * NB + c0 + q < N) cacc_mul(acc[i], ld4(__ldg(up + q)), wc[q]);
+          if (jb < mc - 1) pf_l1(up - NB);   // the next block's operands of this row
         }
+      }
+      // operands of this CTA's next critical step (block m - 2) into L1
+      if (m - 2 >= 0 && (m - 2) % CL == rank) {
+        pf_l1(L + (size_t)((m - 2) * NB + rb) * N + (m - 1) * NB + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pf_l1(D + (size_t)((m - 2) * NB + c0 + q) * NB + rb);
       }
     }
   }
-  // no CTA leaves while copies to or from it may still be in flight
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   __syncthreads();
   cluster_sync();
+  if (*(volatile int*)c.abort_flag) {
+    // a wait gave up: stores from other CTAs may still be landing in this CTA's shared memory,
+    // which outlives none of them only after they complete; they take microseconds, so linger
+    const unsigned long long t0 = gtime_ns();
+    while (gtime_ns() - t0 < 200000ull) {
+    }
+  }
 }
 
 size_t cluster_solve_smem(int N) { return clayout_bytes((N + NB - 1) / NB); }
