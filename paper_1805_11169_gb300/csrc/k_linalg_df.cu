@@ -823,12 +823,14 @@ struct CLayout {
   float4* ws;        // nblk*32 backward solution
   float4* yown;      // CRPC*32 right-hand side of the own rows (double-floats)
   cdf* vsh;          // 32: right-hand side minus products, for the diagonal-block product
+  cacc* acc;         // [CRPC][CTH]: each thread's partial sums of the own block rows
   uint64_t* barF;    // nblk
   uint64_t* barB;    // nblk
   int* abort_flag;
 };
 __host__ __device__ inline size_t clayout_bytes(int nblk) {
-  return (size_t)(2 * nblk + CRPC + 1) * NB * 16 + (size_t)2 * nblk * 8 + 16;
+  return (size_t)(2 * nblk + CRPC + 1) * NB * 16 + (size_t)CRPC * CTH * sizeof(cacc) +
+         (size_t)2 * nblk * 8 + 16;
 }
 __device__ __forceinline__ CLayout clayout(unsigned char* base, int nblk) {
   CLayout c;
@@ -836,7 +838,8 @@ __device__ __forceinline__ CLayout clayout(unsigned char* base, int nblk) {
   c.ws = c.zs + nblk * NB;
   c.yown = c.ws + nblk * NB;
   c.vsh = (cdf*)(c.yown + CRPC * NB);
-  c.barF = (uint64_t*)(c.vsh + NB);
+  c.acc = (cacc*)(c.vsh + NB);
+  c.barF = (uint64_t*)(c.acc + CRPC * CTH);
   c.barB = c.barF + nblk;
   c.abort_flag = (int*)(c.barB + nblk);
   return c;
@@ -938,18 +941,15 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
   __syncthreads();
   cluster_sync();
 
-  cacc acc[CRPC];
+  // the partial sums live in shared memory, so the loops over own rows stay rolled (code size:
+  // the critical path must not miss in the instruction cache after each accumulation sweep)
+  cacc* acc = c.acc + threadIdx.x;           // acc[i * CTH]
   cdf dk[4], lk[4];
   // ------------------------------------------------ forward: L z = y
-#pragma unroll
-  for (int i = 0; i < CRPC; ++i) acc[i] = cacc_zero();
+  for (int i = 0; i < CRPC; ++i) acc[i * CTH] = cacc_zero();
   bool alive = true;
-  if (rank == 0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dk[q] = rb < N ? ld4(D[(size_t)rb * NB + c0 + q]) : czero();
-    finish_block<true>(c, N, 0, cacc_zero(), dk, out, minus_i);
-  }
-  for (int m = 0; m < nblk; ++m) {
+  // m = -1 only finishes block 0 (no products); each finish has a single call site per pass
+  for (int m = -1; m < nblk; ++m) {
     const int mc = m + 1;
     const bool crit = mc < nblk && mc % CL == rank;
     if (crit) {
@@ -957,34 +957,38 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
       const int row = mc * NB + rb;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        lk[q] = row < N ? ld4(__ldg(L + (size_t)row * N + m * NB + c0 + q)) : czero();
+        lk[q] = (m >= 0 && row < N) ? ld4(__ldg(L + (size_t)row * N + m * NB + c0 + q)) : czero();
         dk[q] = row < N ? ld4(__ldg(D + (size_t)row * NB + c0 + q)) : czero();
       }
     }
-    if (!cta_wait_block(c, c.barF + m, status)) { alive = false; break; }
     cdf zc[4];
+    if (m >= 0) {
+      if (!cta_wait_block(c, c.barF + m, status)) { alive = false; break; }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) zc[q] = ld4(c.zs[m * NB + c0 + q]);
+      for (int q = 0; q < 4; ++q) zc[q] = ld4(c.zs[m * NB + c0 + q]);
+    }
     if (crit) {
-      cacc mine = cacc_zero();
+      cacc mine = acc[(mc / CL) * CTH];
+      if (m >= 0) {
 #pragma unroll
-      for (int i = 0; i < CRPC; ++i) if (rank + CL * i == mc) mine = acc[i];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) cacc_mul(mine, lk[q], zc[q]);
+        for (int q = 0; q < 4; ++q) cacc_mul(mine, lk[q], zc[q]);
+      }
       finish_block<true>(c, N, mc, mine, dk, out, minus_i);
     }
+    if (m < 0) continue;
     // the remaining own rows jb > m + 1: acc += L[jb, m] z_m
-#pragma unroll
-    for (int i = 0; i < CRPC; ++i) {
+#pragma unroll 1
+    for (int i = (mc + 1 - rank + CL - 1) / CL; i < CRPC; ++i) {
       const int jb = rank + CL * i;
       const int row = jb * NB + rb;
-      if (jb > mc && jb < nblk && row < N) {
-        const float4* lp = L + (size_t)row * N + m * NB + c0;
+      if (jb >= nblk || row >= N) break;
+      const float4* lp = L + (size_t)row * N + m * NB + c0;
+      cacc a = acc[i * CTH];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cacc_mul(acc[i], ld4(__ldg(lp + q)), zc[q]);
-        // the next block's operands of this row, into L1 while the CTA waits for that block
-        if (jb > mc + 1) pf_l1(lp + NB);
-      }
+      for (int q = 0; q < 4; ++q) cacc_mul(a, ld4(__ldg(lp + q)), zc[q]);
+      acc[i * CTH] = a;
+      // the next block's operands of this row, into L1 while the CTA waits for that block
+      if (jb > mc + 1) pf_l1(lp + NB);
     }
     // operands of this CTA's next critical step (block m + 2 at the next arrival) into L1 now:
     // that step starts right after its block arrives, too soon to wait for L2
@@ -998,18 +1002,9 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
   }
   // ------------------------------------------------ backward: L^H w = z
   if (alive) {
-#pragma unroll
-    for (int i = 0; i < CRPC; ++i) acc[i] = cacc_zero();
-    const int last = nblk - 1;
-    if (last % CL == rank) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = last * NB + c0 + q;
-        dk[q] = r < N ? ld4(D[(size_t)r * NB + rb]) : czero();
-      }
-      finish_block<false>(c, N, last, cacc_zero(), dk, out, minus_i);
-    }
-    for (int m = last; m >= 0; --m) {
+    for (int i = 0; i < CRPC; ++i) acc[i * CTH] = cacc_zero();
+    // m = nblk only finishes the last block
+    for (int m = nblk; m >= 0; --m) {
       const int mc = m - 1;
       const bool crit = mc >= 0 && mc % CL == rank;
       if (crit) {
@@ -1017,33 +1012,38 @@ k_chol_solve_cluster(int N, const float4* __restrict__ L, const float4* __restri
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int rm = m * NB + c0 + q;
-          lk[q] = rm < N ? ld4(__ldg(L + (size_t)(mc * NB + rb) * N + rm)) : czero();
-          dk[q] = ld4(__ldg(D + (size_t)(mc * NB + c0 + q) * NB + rb));
+          const int rd = mc * NB + c0 + q;
+          lk[q] = (m < nblk && rm < N) ? ld4(__ldg(L + (size_t)(mc * NB + rb) * N + rm)) : czero();
+          dk[q] = rd < N ? ld4(__ldg(D + (size_t)rd * NB + rb)) : czero();
         }
       }
-      if (!cta_wait_block(c, c.barB + m, status)) break;
       cdf wc[4];
+      if (m < nblk) {
+        if (!cta_wait_block(c, c.barB + m, status)) break;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) wc[q] = ld4(c.ws[m * NB + c0 + q]);
+        for (int q = 0; q < 4; ++q) wc[q] = ld4(c.ws[m * NB + c0 + q]);
+      }
       if (crit) {
-        cacc mine = cacc_zero();
+        cacc mine = acc[(mc / CL) * CTH];
+        if (m < nblk) {
 #pragma unroll
-        for (int i = 0; i < CRPC; ++i) if (rank + CL * i == mc) mine = acc[i];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cacc_mul(mine, lk[q], wc[q]);
+          for (int q = 0; q < 4; ++q) cacc_mul(mine, lk[q], wc[q]);
+        }
         finish_block<false>(c, N, mc, mine, dk, out, minus_i);
       }
+      if (m >= nblk) continue;
       // the remaining own rows jb < m - 1: acc += (L^H)[jb, m] w_m, read by rows of the upper triangle
-#pragma unroll
+#pragma unroll 1
       for (int i = 0; i < CRPC; ++i) {
         const int jb = rank + CL * i;
-        if (jb < mc) {
-          const float4* up = L + (size_t)(jb * NB + rb) * N + m * NB + c0;
+        if (jb >= mc) break;
+        const float4* up = L + (size_t)(jb * NB + rb) * N + m * NB + c0;
+        cacc a = acc[i * CTH];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (m * NB + c0 + q < N) cacc_mul(acc[i], ld4(__ldg(up + q)), wc[q]);
-          if (jb < mc - 1) pf_l1(up - NB);   // the next block's operands of this row
-        }
+        for (int q = 0; q < 4; ++q)
+          if (m * NB + c0 + q < N) cacc_mul(a, ld4(__ldg(up + q)), wc[q]);
+        acc[i * CTH] = a;
+        if (jb < mc - 1) pf_l1(up - NB);   // the next block's operands of this row
       }
       // operands of this CTA's next critical step (block m - 2) into L1
       if (m - 2 >= 0 && (m - 2) % CL == rank) {
