@@ -153,6 +153,9 @@ constexpr int CS_THREADS = 256;
 constexpr int TS_ROWS = 8;                    // panel rows per slab task
 constexpr unsigned CS_WAIT_LIMIT = 1u << 24;
 constexpr int CS_SMEM = 6 * NB * NB * 8;      // largest task: trailing tile, 6 double-float planes
+// shared memory requested per CTA: more than the tasks use, so that at most two CTAs share an SM
+// and the dependency chain (diagonal factor, panel slabs) is not starved by trailing tiles
+constexpr int CS_SMEM_LAUNCH = 100 * 1024;
 
 __device__ __forceinline__ cdf ldcg4(const float4* p) { return ld4(__ldcg(p)); }
 __device__ __forceinline__ cdf cdf_sub_sloppy(cdf a, cdf b) {
@@ -1091,7 +1094,7 @@ int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, 
   const int T = (N + NB - 1) / NB;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_chol_step_df, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM);
+    cudaFuncSetAttribute(k_chol_step_df, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_SMEM_LAUNCH);
     attr = true;
   }
   cudaMemsetAsync(ctl, 0, chol_ctl_words(N) * sizeof(unsigned), s);
@@ -1102,7 +1105,7 @@ int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, 
     const int rows = N - (li + 1) * NB;
     const int nslab = (li < T && rows > 0) ? (rows + TS_ROWS - 1) / TS_ROWS : 0;
     const int per = (jb >= 0 && li < T ? 3 : 0) + (li < T ? 1 : 0) + (li >= 1 ? 1 : 0) + nherk + nslab;
-    k_chol_step_df<<<nbatch * per, CS_THREADS, CS_SMEM, s>>>(N, mb, nbatch, li, ctl, status);
+    k_chol_step_df<<<nbatch * per, CS_THREADS, CS_SMEM_LAUNCH, s>>>(N, mb, nbatch, li, ctl, status);
   }
   return T + 2;
 }
