@@ -104,6 +104,12 @@ def max_over_ranks(v, ws):
     return float(t.item())
 
 
+def whole_job_rate(ws, units_per_rank, slowest_s):
+    """Whole-job throughput of ws independent replicas: all ranks' units over the slowest rank's
+    time (every rank runs the same workload; the job ends when the last one does)."""
+    return ws * units_per_rank / slowest_s
+
+
 # ---------------------------------------------------------------- clocks
 
 class Clocks:
@@ -269,7 +275,7 @@ def run_ours(args, rank, ws, local):
     n_obs = args.steps // OBS_EVERY
     obs_launches = 4 * n_obs
     total_s = max_over_ranks(sum(step_ms) / 1e3, ws)
-    value = ws * w.n_traj * args.steps / total_s
+    value = whole_job_rate(ws, w.n_traj * args.steps, total_s)
     sim.close()
 
     peaks = {}
