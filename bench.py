@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="tf32x3", choices=list(MODES))
+    ap.add_argument("--no-exact2d", action="store_true",
+                    help="skip the exact 2D propagation measurement on the same grid")
     ap.add_argument("--solve", default="df64", choices=["df64", "fp64"],
                     help="mixed modes: Cholesky and triangular solves in double-float (default) "
                          "or FP64")
@@ -316,6 +319,8 @@ def run_ours(args, rank, ws, local):
     if rank == 0 and not args.no_fp64 and args.mode != "fp64":
         out["fp64"] = run_fp64_comparison()
         out["speedup_vs_fp64"] = value / out["fp64"]["value"]
+    if rank == 0 and not args.no_exact2d:
+        out["exact2d"] = run_exact2d(w)
     if rank == 0 and args.serving_jobs > 0:
         out["serving"] = run_serving(args.serving_jobs)
     if rank == 0 and not args.no_cpu:
@@ -376,6 +381,27 @@ def run_cpu_baseline(w, budget_s):
 
 
 # ---------------------------------------------------------------- FP64 comparison and serving
+
+def run_exact2d(w, steps=50, warmup=2):
+    """The exact Strang propagation of Psi(x, R) on the GPU (FP64) on the bench grid: grid
+    points x steps / s, with its FP64 roofline (two 2D FFTs of 5 n log2 n flops and ~24 flops of
+    phases per point and step)."""
+    import paper_1805_11169_gb300 as g
+    e = g.Exact2D(g.params_from(w), w.V)
+    e.set_state(w.psi0)
+    e.step(warmup)
+    t0 = time.perf_counter()
+    e.step(steps)
+    dt = time.perf_counter() - t0
+    e.close()
+    n = w.nx * w.nR
+    flops = 2 * 5.0 * n * math.log2(n) + 24.0 * n
+    return {"value": n * steps / dt, "unit": "grid-point-steps/s", "ms_per_step": 1e3 * dt / steps,
+            "grid": [w.nx, w.nR], "steps": steps, "dtype": "f64",
+            "roofline": {"bound": "alu", "achieved": flops * steps / dt / 1e12,
+                         "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops * steps / dt / 1e12 / NOMINAL_FP64_TFLOPS}}
+
 
 def run_fp64_comparison(steps=10, warmup=2):
     """The same workload in FP64 mode (same GB300, same process): trajectory-steps/s."""

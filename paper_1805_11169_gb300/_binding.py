@@ -80,6 +80,13 @@ def _load():
         "icwf_pool_tick": [H, P(ct.c_int32), P(ct.c_int32)],
         "icwf_pool_poll": [H, ct.c_int32, P(icwf_obs), P(ct.c_int32)],
         "icwf_pool_destroy": [H],
+        "icwf_exact2d_create": [P(icwf_params), d, P(H)],
+        "icwf_exact2d_set_state": [H, d],
+        "icwf_exact2d_set_projectors": [H, ct.c_int32, d],
+        "icwf_exact2d_step": [H, ct.c_int32],
+        "icwf_exact2d_get_state": [H, d],
+        "icwf_exact2d_observables": [H, P(icwf_obs)],
+        "icwf_exact2d_destroy": [H],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -87,6 +94,8 @@ def _load():
         f.restype = ct.c_int
     lib.icwf_last_error.argtypes = [H]
     lib.icwf_last_error.restype = ct.c_char_p
+    lib.icwf_exact2d_last_error.argtypes = [H]
+    lib.icwf_exact2d_last_error.restype = ct.c_char_p
     return lib
 
 
@@ -336,3 +345,70 @@ class Icwf:
         """Give up ownership (after icwf_pool_submit the pool owns the handle)."""
         h, self.h = self.h, None
         return h
+
+
+# ---- exact 2D propagation (include/icwf_exact2d.h) ---------------------------------------------
+
+def _check2(st, h=None):
+    if st != ICWF_OK:
+        raise IcwfError(st, LIB.icwf_exact2d_last_error(h).decode())
+
+
+def icwf_exact2d_create(params: icwf_params, V: np.ndarray):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    assert V.shape == (params.nx, params.nR)
+    h = ct.c_void_p()
+    _check2(LIB.icwf_exact2d_create(ct.byref(params), _dp(V), ct.byref(h)))
+    return h
+
+
+class Exact2D:
+    """The exact Strang-split propagation of Psi(x, R) on the GPU (FP64), same grid, masses, V
+    and dt as an ICWF parameter set."""
+
+    def __init__(self, params: icwf_params, V: np.ndarray):
+        self.nx, self.nR = params.nx, params.nR
+        self.h = icwf_exact2d_create(params, V)
+        self.n_states = 0
+
+    def set_state(self, psi: np.ndarray):
+        psi = _c128(psi, (self.nx, self.nR))
+        _check2(LIB.icwf_exact2d_set_state(self.h, psi.ctypes.data_as(ct.POINTER(ct.c_double))),
+                self.h)
+
+    def set_projectors(self, phi: np.ndarray):
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        _check2(LIB.icwf_exact2d_set_projectors(self.h, phi.shape[0], _dp(phi)), self.h)
+        self.n_states = phi.shape[0]
+
+    def step(self, n: int = 1):
+        _check2(LIB.icwf_exact2d_step(self.h, n), self.h)
+
+    def state(self) -> np.ndarray:
+        out = np.empty((self.nx, self.nR), dtype=np.complex128)
+        _check2(LIB.icwf_exact2d_get_state(self.h, out.ctypes.data_as(ct.POINTER(ct.c_double))),
+                self.h)
+        return out
+
+    def observables(self) -> dict:
+        rx, rR = np.empty(self.nx), np.empty(self.nR)
+        ns = max(self.n_states, 1)
+        pop, dec = np.zeros(ns), np.zeros(ns * ns)
+        o = icwf_obs(rho_x=_dp(rx), rho_R=_dp(rR), pop=_dp(pop), decoh=_dp(dec))
+        _check2(LIB.icwf_exact2d_observables(self.h, ct.byref(o)), self.h)
+        out = dict(t=o.t, norm=o.norm, energy=o.energy, rho_x=rx, rho_R=rR)
+        if self.n_states:
+            out["pop"] = pop[:self.n_states]
+            out["decoherence"] = dec.reshape(ns, ns)[:self.n_states, :self.n_states]
+        return out
+
+    def close(self):
+        if self.h is not None:
+            LIB.icwf_exact2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -156,6 +156,7 @@ constexpr int CS_SMEM = 6 * NB * NB * 8;      // largest task: trailing tile, 6 
 // shared memory requested per CTA: more than the tasks use, so that at most two CTAs share an SM
 // and the dependency chain (diagonal factor, panel slabs) is not starved by trailing tiles
 constexpr int CS_SMEM_LAUNCH = 100 * 1024;
+static_assert(CS_SMEM <= CS_SMEM_LAUNCH, "tasks need more shared memory than the launch asks for");
 
 __device__ __forceinline__ cdf ldcg4(const float4* p) { return ld4(__ldcg(p)); }
 __device__ __forceinline__ cdf cdf_sub_sloppy(cdf a, cdf b) {

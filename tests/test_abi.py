@@ -1,4 +1,4 @@
-"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/icwf.h declares
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/*.h declares
 (CPU only: no compute call is made)."""
 import ctypes
 import os
@@ -10,7 +10,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    txt = open(os.path.join(ROOT, "include", "icwf.h")).read()
+    inc = os.path.join(ROOT, "include")
+    txt = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                  if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(icwf_[a-z_0-9]+)\s*\(", txt)))
 
@@ -61,3 +63,20 @@ def test_null_handle_calls_are_rejected(lib):
     assert g.LIB.icwf_step(None, 1) == g.ICWF_ERR_ARG
     assert g.LIB.icwf_destroy(None) == g.ICWF_OK
     assert g.LIB.icwf_pool_destroy(None) == g.ICWF_OK
+
+
+def test_exact2d_rejects_bad_arguments_without_a_gpu(lib):
+    import numpy as np
+    import paper_1805_11169_gb300 as g
+    p = g.icwf_params(nx=100, nR=64, x_min=-1, x_max=1, R_min=-1, R_max=1, mass_x=1, mass_R=1,
+                      dt=0.1)
+    with pytest.raises(g.IcwfError) as e:
+        g.icwf_exact2d_create(p, np.zeros((100, 64)))
+    assert e.value.status == g.ICWF_ERR_ARG and "powers of two" in str(e.value)
+    p.nx = 64
+    p.mass_R = 0.0
+    with pytest.raises(g.IcwfError) as e:
+        g.icwf_exact2d_create(p, np.zeros((64, 64)))
+    assert e.value.status == g.ICWF_ERR_ARG
+    assert g.LIB.icwf_exact2d_step(None, 1) == g.ICWF_ERR_ARG
+    assert g.LIB.icwf_exact2d_destroy(None) == g.ICWF_OK
