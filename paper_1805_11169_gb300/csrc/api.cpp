@@ -484,7 +484,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   if (p.precision < 0 || p.precision > 2)
     return fail(nullptr, ICWF_ERR_ARG, "icwf_create: unknown precision");
   if (p.precision != ICWF_FP64 && assemble_tc_scratch_bytes(p.n_traj, p.nx, p.nR, 1) == 0)
-    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: mixed precision is not available in this build");
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: mixed precision is not available in this library");
   if (p.coeff_scheme < 0 || p.coeff_scheme > 1)
     return fail(nullptr, ICWF_ERR_ARG, "icwf_create: unknown coeff_scheme");
   const size_t nV = (size_t)p.nx * p.nR;
