@@ -3,9 +3,10 @@
 // Knuth (TwoSum), Dekker (FastTwoSum) and the FMA-based exact product (TwoProduct), as in
 // Dekker 1971 and the GPU double-float literature (e.g. Thall 2006).
 //
-// Used only where FP64's instruction latency would sit on a long dependency chain (the 32 x 32
-// diagonal-block Cholesky and its inverse): FP32 operations have a small fraction of the FP64
-// latency on this GPU.  Inputs and outputs of those kernels stay FP64.
+// Used where FP64's instruction latency or throughput would bound a dependency chain: inside the
+// FP64 mode's 32 x 32 diagonal-block Cholesky (inputs and outputs FP64), and for the whole
+// factorisation and triangular solves of the mixed modes (k_linalg_df.cu).  FP32 operations have
+// a small fraction of the FP64 latency and ~60x its throughput on this GPU.
 //
 // Every operation is spelled with explicit round-to-nearest intrinsics on the device so that the
 // compiler cannot contract or reassociate them (that would break the error-free transformations);

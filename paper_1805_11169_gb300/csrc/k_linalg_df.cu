@@ -9,8 +9,12 @@
 // style of Ogita, Rump and Oishi's Dot2 (TwoProduct + TwoSum, errors summed separately), which
 // returns them as accurately as if evaluated in twice the FP32 precision.
 //
-// Kernels mirror the FP64 ones in k_linalg.cu: shift (S -> S + eps I, converted), diagonal factor,
-// panel solve, trailing update, diagonal-block inverses, forward / backward triangular solves.
+// Kernels: k_shift_mix_df (S -> S + eps I, converted); k_chol_step_df (the blocked Cholesky, one
+// launch per block column with look-ahead: quadrant updates, diagonal factor, panel slabs,
+// trailing tiles and the inverses of the diagonal blocks as ticket-ordered tasks; the panel tasks
+// also write L^H into the upper triangle); k_chol_solve_cluster (both triangular solves in one
+// 8-CTA cluster, N <= 2048) and k_trsv_lower_df / k_trsv_upper_df (per-block kernels with global
+// flags, larger N).
 #include <cuda_runtime.h>
 
 #include "df64.cuh"
