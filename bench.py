@@ -57,6 +57,9 @@ def parse():
                     help="also run ICWF and the exact 2D propagation side by side for STEPS steps "
                          "and report density and population errors ('vs_exact'); not timed")
     ap.add_argument("--vs-exact-every", type=int, default=2000)
+    ap.add_argument("--coeff-scheme", default="interpolated", choices=["interpolated", "frozen"],
+                    help="RK4 with S, Heff linear over the step (two factorisations per step, "
+                         "default) or frozen at t_n (one)")
     ap.add_argument("--no-exact2d", action="store_true",
                     help="skip the exact 2D propagation measurement on the same grid")
     ap.add_argument("--solve", default="df64", choices=["df64", "fp64"],
@@ -178,7 +181,7 @@ class Clocks:
 
 # ---------------------------------------------------------------- roofline bookkeeping
 
-def algorithmic_work(fam, w, K, mode):
+def algorithmic_work(fam, w, K, mode, nfact=2):
     """(amount, unit, bound) of algorithmic work per launch of a kernel family."""
     N, nx, nR = w.n_traj, w.nx, w.nR
     c = 16 if mode == "fp64" else 8
@@ -188,8 +191,9 @@ def algorithmic_work(fam, w, K, mode):
     if fam == "propagate":
         return 2.0 * N * (nx + nR) * c, "byte", "hbm"
     if fam == "cholesky":
-        # one call factors S(t+dt/2) and S(t+dt) together: 2 x (4/3) N^3 (complex Cholesky)
-        return 2 * 4.0 / 3.0 * N ** 3, "flop", "alu"
+        # one call factors S(t+dt/2) and S(t+dt) together (interpolated scheme; the frozen one
+        # factors S(t+dt) alone): nfact x (4/3) N^3 (complex Cholesky)
+        return nfact * 4.0 / 3.0 * N ** 3, "flop", "alu"
     if fam == "velocity":
         return 2.0 * 4 * N * N * c, "byte", "hbm"
     if fam == "rk4_matvec":
@@ -199,10 +203,10 @@ def algorithmic_work(fam, w, K, mode):
     return None
 
 
-def roofline(prof, w, K, mode, peaks, solve="df64"):
+def roofline(prof, w, K, mode, peaks, solve="df64", nfact=2):
     fam = max(prof, key=lambda f: prof[f][0])
     ms, n = prof[fam]
-    work = algorithmic_work(fam, w, K, mode)
+    work = algorithmic_work(fam, w, K, mode, nfact)
     out = {"kernel": fam, "launches": n, "avg_ms": ms / max(n, 1)}
     if work is None or n == 0:
         return out
@@ -247,7 +251,8 @@ def run_ours(args, rank, ws, local):
     torch.cuda.set_device(local)
     prec, dtype_name, cutoff, eps = MODES[args.mode]
     w = make_workload(args.n_traj, cutoff, eps, args.nx, args.nR)
-    params = g.params_from(w, precision=prec, solve_fp64=int(args.solve == "fp64"))
+    params = g.params_from(w, precision=prec, solve_fp64=int(args.solve == "fp64"),
+                           coeff_scheme=int(args.coeff_scheme == "frozen"))
 
     sim = g.Icwf(params, w.V)
     sim.set_projectors(w.phi)
@@ -293,7 +298,8 @@ def run_ours(args, rank, ws, local):
     except (OSError, ValueError):
         peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
     prof_step = {f: v for f, v in prof.items() if v[1] > 0 and f != "observables"}
-    rl = roofline(prof_step, w, info["rank"], args.mode, peaks, args.solve)
+    rl = roofline(prof_step, w, info["rank"], args.mode, peaks, args.solve,
+                  1 if args.coeff_scheme == "frozen" else 2)
 
     out = {
         "metric": "ICWF trajectory-steps/s at N=1024",
@@ -310,7 +316,7 @@ def run_ours(args, rank, ws, local):
         "data": "synthetic (Shin-Metiu potential, BO states and |Psi0|^2 sampling computed here)",
         "config": {"workload": workload_name(w), "nx": w.nx, "nR": w.nR, "n_traj": w.n_traj,
                    "dt": w.dt, "rank_k": info["rank"], "svd_rel_cutoff": cutoff, "s_reg_eps": eps,
-                   "svd_tail_rel": info["tail_rel"], "coeff_scheme": "rk4-interpolated",
+                   "svd_tail_rel": info["tail_rel"], "coeff_scheme": "rk4-" + args.coeff_scheme,
                    "solve": ("fp64" if args.mode == "fp64" or args.solve == "fp64"
                              else "double-float (FP32 pairs)"),
                    "obs_every": OBS_EVERY, "l2": "flushed (256 MB write) before every timed step",
