@@ -342,9 +342,11 @@ icwf_status icwf_exact2d_create(const icwf_params* p, const double* V, icwf_exac
     delete h;
     return fail2(nullptr, ICWF_ERR_CUDA, "icwf_exact2d_create: upload failed");
   }
-  const int smr = h->nR * (int)sizeof(double2), smc = h->CB * h->nx * (int)sizeof(double2);
-  cudaFuncSetAttribute(e2d::k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smr);
-  cudaFuncSetAttribute(e2d::k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
+  // the largest dynamic shared memory any handle uses (nR <= 4096 rows, CB * nx <= 96 KB), so
+  // that handles of different sizes can coexist
+  cudaFuncSetAttribute(e2d::k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       4096 * (int)sizeof(double2));
+  cudaFuncSetAttribute(e2d::k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   *out = h;
   return ICWF_OK;
 }

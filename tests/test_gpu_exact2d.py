@@ -81,3 +81,21 @@ def test_call_order_and_sizes():
         e.set_projectors(np.zeros((9, w.nR, w.nx)))
     assert ex.value.status == g.ICWF_ERR_ARG
     e.close()
+
+
+def test_handles_of_different_sizes_coexist():
+    """A small handle created after a large one must not break the large one's launches."""
+    from workloads.models import WORKLOADS
+    big = WORKLOADS["sm_paper"](n_traj=8)
+    small = shin_metiu()
+    eb = g.Exact2D(g.params_from(big), big.V)
+    eb.set_state(big.psi0)
+    es = g.Exact2D(g.params_from(small), small.V)
+    es.set_state(small.psi0)
+    eb.step(2)
+    es.step(2)
+    ref = _oracle(big).run(big.psi0, 2)
+    assert _rel(eb.state(), ref) < 1e-11
+    eb.close()
+    es.close()
+
