@@ -235,7 +235,9 @@ class Icwf:
     def velocities(self, st: State):
         """Eq. v1/v2: xdot_a = Im[sum_b C_b chi_b(R_a) psi_b'(x_a) / Psi(x_a, R_a)] / m_x and
         Rdot_a = Im[sum_b C_b psi_b(x_a) chi_b'(R_a) / Psi(x_a, R_a)] / m_R, with
-        Psi(x_a, R_a) = sum_b C_b psi_b(x_a) chi_b(R_a)."""
+        Psi(x_a, R_a) = sum_b C_b psi_b(x_a) chi_b(R_a).
+        Parity pinned: a moving Gaussian (1/m and the sign of Im) and two boosted Gaussians with
+        unequal complex C against the closed-form Im(grad Psi / Psi) / m (tests)."""
         p = self.p
         vx = np.empty(p.n_traj)
         vR = np.empty(p.n_traj)
@@ -327,7 +329,9 @@ class Icwf:
 
     def rk4(self, C, S0, H0, S1, H1):
         """Classical RK4 on dC/dt = -i (S(t) + eps I)^-1 Heff(t) C (Eq. coeff) over one dt, with
-        S and Heff linear in t between their values at t_n (S0, H0) and t_{n+1} (S1, H1)."""
+        S and Heff linear in t between their values at t_n (S0, H0) and t_{n+1} (S1, H1).
+        Parity pinned: constant matrices against the matrix exponential, and matrices linear in t
+        against an independent adaptive integrator, both at fourth order (tests)."""
         dt = self.p.dt
         Sh = 0.5 * (S0 + S1)
         Hh = 0.5 * (H0 + H1)
@@ -415,6 +419,9 @@ def grid_observables(Psi, V, dx, dR, kx, kR, mass_x, mass_R, phi=None) -> dict:
     chi^(n)(R) = int dx phi_n(x; R) Psi(x, R) for real BO states phi (n_s x nR x nx),
     P_n = int dR |chi^(n)|^2 (BO populations), D_nm = int dR |chi^(n)|^2 |chi^(m)|^2 (decoherence
     indicator defined in the paper's discussion of the Shin-Metiu results).
+    Parity pinned: norm and energy against the matrix forms C^H S C and C^H H C; populations,
+    D_nm and rho_R against the closed forms of g(R) phi_1 and of a two-state superposition a(R)
+    phi_0 + b(R) phi_2 (BO states orthonormal at every R) (tests).
     """
     nx, nR = Psi.shape
     dens = Psi.real ** 2 + Psi.imag ** 2

@@ -381,3 +381,149 @@ def test_observables_agree_with_matrix_forms():
     assert np.all(ob["pop"] >= 0) and ob["pop"].sum() <= ob["norm"] + 1e-12
     D = ob["decoherence"]
     assert np.allclose(D, D.T) and np.all(D >= 0)
+
+
+# ---------------------------------------------------------------- populations and decoherence
+
+def _bo_superposition(w, a_of_R, b_of_R, n_lo=0, n_hi=2):
+    """Psi(x, R) = a(R) phi_lo(x; R) + b(R) phi_hi(x; R) on the workload's grid."""
+    return (a_of_R[None, :] * w.phi[n_lo].T + b_of_R[None, :] * w.phi[n_hi].T).astype(complex)
+
+
+def _closed_form_pop(w, a_of_R, b_of_R, n_lo=0, n_hi=2):
+    """The BO states are orthonormal on the x grid at every R_j, so chi^(lo) = a, chi^(hi) = b,
+    the third projection vanishes, rho_R = |a|^2 + |b|^2, P_n = int dR |chi^(n)|^2 and
+    D_nm = int dR |chi^(n)|^2 |chi^(m)|^2 (the Shin-Metiu discussion's indicator)."""
+    ns = w.phi.shape[0]
+    chin = np.zeros((ns, w.nR), complex)
+    chin[n_lo] = a_of_R
+    chin[n_hi] = b_of_R
+    pn = np.abs(chin) ** 2
+    return pn.sum(axis=1) * w.dR, w.dR * (pn[:, None, :] * pn[None, :, :]).sum(axis=2), \
+        np.abs(a_of_R) ** 2 + np.abs(b_of_R) ** 2
+
+
+def _assert_obs(ob, pop, D, rhoR):
+    assert np.max(np.abs(ob["pop"] - pop)) < 1e-12
+    assert np.max(np.abs(ob["decoherence"] - D)) < 1e-12 * max(1.0, np.max(D))
+    assert np.max(np.abs(ob["rho_R"] - rhoR)) < 1e-12 * np.max(rhoR)
+
+
+def test_initial_state_populations_and_decoherence_closed_form():
+    """Psi0 = g(R) phi_1(x; R) (the Shin-Metiu initial state) has P = (0, 1, 0) and
+    D_11 = int dR |g|^4 with g the normalised nuclear Gaussian, every other D_nm zero; checked
+    through the exact solver's observables and through an ICWF state whose basis reproduces
+    Psi0 (chi_a = grid delta at R_a, psi_a = g(R_a) phi_1(.; R_a))."""
+    w = _tiny_sm()
+    g = np.exp(-((w.R - w.model["R0"]) ** 2) / (2.0 * w.model["width"] ** 2))
+    g = g / np.sqrt(w.dR * np.sum(g ** 2))
+    pop, D, rhoR = _closed_form_pop(w, np.zeros(w.nR), g, n_lo=0, n_hi=1)
+    assert abs(pop[1] - 1.0) < 1e-12 and abs(D[1, 1] - w.dR * np.sum(g ** 4)) < 1e-15
+    ex = Exact2D(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, w.dt, w.V)
+    _assert_obs(ex.observables(w.psi0, w.phi), pop, D, rhoR)
+    o = Icwf(_params(w, n_traj=w.nR), w.V)
+    theta = np.linspace(0.3, 2.9, w.nR)                        # complex C, compensated in psi
+    psi = (w.phi[1].T * (g * np.exp(-1j * theta))[None, :])   # column a = g(R_a) phi_1(x; R_a)
+    chi = np.eye(w.nR, dtype=complex)                          # chi_a(R_j) = delta_aj
+    st = State(psi=psi, chi=chi, C=np.exp(1j * theta), x=np.zeros(w.nR), R=w.R.copy(),
+               S=None, Heff=None)
+    assert np.max(np.abs(o.wavefunction(st) - w.psi0)) < 1e-13 * np.max(np.abs(w.psi0))
+    _assert_obs(o.observables(st, w.phi), pop, D, rhoR)
+
+
+def test_superposition_populations_and_decoherence_closed_form():
+    """Psi = a(R) phi_0 + b(R) phi_2 with unequal complex nuclear factors: P_0 = int |a|^2,
+    P_1 = 0, P_2 = int |b|^2, D_02 = int |a|^2 |b|^2 dR (a dropped dx, a transposed projector or
+    a wrong squared modulus fails)."""
+    w = _tiny_sm()
+    a = np.exp(-((w.R + 2.0) ** 2) / 2.0) * np.exp(0.7j * w.R)
+    b = 0.6 * np.exp(-((w.R - 1.0) ** 2) / 3.0) * (1.0 - 0.4j * w.R)
+    pop, D, rhoR = _closed_form_pop(w, a, b)
+    assert pop[1] == 0.0 and D[0, 2] > 1e-3 and abs(pop[0] - pop[2]) > 0.1
+    Psi = _bo_superposition(w, a, b)
+    ex = Exact2D(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, w.dt, w.V)
+    ob = ex.observables(Psi, w.phi)
+    _assert_obs(ob, pop, D, rhoR)
+    assert abs(ob["norm"] - (pop[0] + pop[2])) < 1e-12
+
+
+# ---------------------------------------------------------------- velocities, several terms
+
+def test_velocity_of_two_boosted_gaussians():
+    """N = 2 basis functions psi_b chi_b (Gaussians with their own centres and momenta) and
+    unequal complex C: Eq. v1/v2 at a trajectory's position equals the closed form
+    Im(d_x Psi / Psi) / m_x, Im(d_R Psi / Psi) / m_R with
+    d_x psi_b = (-(x - x_b) / s^2 + i k_b) psi_b.  C does not cancel, so using C_a for C_b, a
+    conjugate, or a factor at the wrong point fails."""
+    nx, nR = 1024, 1024       # cells of 0.02: the stencil's O(dx^3) derivative error ~1e-6
+    mx, mR = 1.0, 40.0
+    p = Params(nx, nR, -10.0, 10.0, -10.0, 10.0, mx, mR, 0.01, 2, 0.0, 1e-10)
+    o = Icwf(p, np.zeros((nx, nR)))
+    s = 1.3
+    xc, kx = np.array([-0.8, 1.1]), np.array([0.9, -0.6])
+    Rc, kR = np.array([0.5, -0.7]), np.array([-1.2, 0.8])
+    C = np.array([0.9 - 0.3j, -0.4 + 0.7j])
+
+    def g(z, zc, k):
+        return np.exp(-((z - zc) ** 2) / (2 * s * s) + 1j * k * z)
+
+    def dg(z, zc, k):
+        return (-(z - zc) / (s * s) + 1j * k) * g(z, zc, k)
+
+    psi = np.stack([g(o.x, xc[b], kx[b]) for b in range(2)], axis=1)
+    chi = np.stack([g(o.R, Rc[b], kR[b]) for b in range(2)], axis=1)
+    rng = np.random.default_rng(9)
+    checked = 0
+    for _ in range(6):
+        xa = rng.uniform(-1.5, 1.5, 2)
+        Ra = rng.uniform(-1.2, 1.2, 2)
+        st = State(psi=psi, chi=chi, C=C, x=xa, R=Ra, S=None, Heff=None)
+        vx, vR = o.velocities(st)
+        for a in range(2):
+            P = sum(C[b] * g(xa[a], xc[b], kx[b]) * g(Ra[a], Rc[b], kR[b]) for b in range(2))
+            Px = sum(C[b] * dg(xa[a], xc[b], kx[b]) * g(Ra[a], Rc[b], kR[b]) for b in range(2))
+            PR = sum(C[b] * g(xa[a], xc[b], kx[b]) * dg(Ra[a], Rc[b], kR[b]) for b in range(2))
+            ex_vx, ex_vR = (Px / P).imag / mx, (PR / P).imag / mR
+            assert abs(vx[a] - ex_vx) < 1e-5 * max(1.0, abs(ex_vx))
+            assert abs(vR[a] - ex_vR) < 1e-5 * max(1.0 / mR, abs(ex_vR))
+            checked += 1
+    assert checked == 12
+
+
+# ---------------------------------------------------------------- RK4 with moving matrices
+
+def test_rk4_with_linear_matrices_matches_fine_integrator():
+    """S(t), Heff(t) linear in t over the whole interval (so the per-step interpolation between
+    the endpoint assemblies is exact): the RK4 of Eq. coeff converges at fourth order to an
+    independent adaptive integrator (scipy DOP853, rtol 1e-12) of dC/dt = -i (S(t) + eps I)^-1
+    Heff(t) C.  Freezing the matrices at t_n, or using the endpoint matrices at the half-step
+    stages, drops the order and fails the ratio."""
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(4)
+    N, T = 4, 0.6
+    A0 = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    A1 = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    S0 = A0.conj().T @ A0 / N + np.eye(N)
+    S1 = A1.conj().T @ A1 / N + np.eye(N)
+    H0 = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    H1 = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    eps = 1e-10
+    St = lambda t: S0 + (t / T) * (S1 - S0)
+    Ht = lambda t: H0 + (t / T) * (H1 - H0)
+    C0 = rng.normal(size=N) + 1j * rng.normal(size=N)
+
+    def rhs(t, c):
+        return -1j * np.linalg.solve(St(t) + eps * np.eye(N), Ht(t) @ c)
+
+    ref = solve_ivp(rhs, (0.0, T), C0, method="DOP853", rtol=1e-12, atol=1e-14).y[:, -1]
+    p = Params(8, 8, 0, 1, 0, 1, 1, 1, 0.01, N, 0.0, eps)
+    o = Icwf(p, np.zeros((8, 8)))
+    errs = []
+    for n in (20, 40):
+        dt = T / n
+        o.p.dt = dt
+        C = C0.copy()
+        for k in range(n):
+            C = o.rk4(C, St(k * dt), Ht(k * dt), St((k + 1) * dt), Ht((k + 1) * dt))
+        errs.append(np.max(np.abs(C - ref)))
+    assert errs[0] < 1e-5 and 12 < errs[0] / errs[1] < 20      # fourth order
