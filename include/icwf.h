@@ -89,6 +89,8 @@ typedef struct {
   int64_t steps_done;       /* completed time steps since init */
   double t;                 /* simulated time */
   int64_t kernel_launches;  /* CUDA kernels launched by icwf_step on this handle since create */
+  size_t obs_bytes;         /* device memory of the observables work buffers, which
+                               icwf_observables allocates on its first call (0 until then) */
 } icwf_info;
 
 /* Observables of the current state (paper: reduced densities, BO populations and the
@@ -180,19 +182,20 @@ const char* icwf_last_error(icwf_handle h);
 #define ICWF_OBS_STATIC_BYTES 9437184u
 #define ICWF_OBS_STATIC_MAX_GRID 524288u
 
-/* Same observables as icwf_observables, computed without allocating any device memory during
- * the call.  For callers that cannot call cudaMalloc while they run: code being captured into a
- * CUDA graph (allocation cannot be captured) or hosts whose allocator forbids device allocation
- * after start-up.  icwf_observables allocates its work buffers on its first call; this entry point
- * uses one fixed work area of ICWF_OBS_STATIC_BYTES bytes compiled into the library as a static
- * device array, which every GPU that loads the library holds until the process exits.  It calls
- * no cudaMalloc, cudaFree or other allocating routine.
+/* Same observables as icwf_observables, computed without allocating any device memory during the
+ * call.  For hosts whose allocator policy forbids device allocation after start-up (an application
+ * that reserves its device memory in one arena when it starts, or a serving path that must not
+ * allocate).  icwf_observables allocates its work buffers on its first call; this entry point uses
+ * one fixed work area of ICWF_OBS_STATIC_BYTES bytes compiled into the library as a static device
+ * array, which every GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  It copies its results into the caller's host
+ * arrays and waits for the handle's stream, so it must be called outside any stream capture.
  * Limits: nx * nR <= ICWF_OBS_STATIC_MAX_GRID and nx, nR <= 4096, else ICWF_ERR_ARG.
  * The first call on a device looks up the work area's device address (once per device, with that
- * device made current for the lookup): make that first call before any stream capture.  All calls
- * share the one work area, so calls that overlap on the GPU (two handles, streams or threads)
- * race; the caller must serialise them.  Each call overwrites every part of the work area that it
- * reads, so nothing left by an earlier call needs clearing.
+ * device made current for the lookup).  All calls share the one work area, so calls that overlap
+ * on the GPU (two handles, streams or threads) race; the caller must serialise them.  Each call
+ * overwrites every part of the work area that it reads, so nothing left by an earlier call needs
+ * clearing.
  * The paper has no counterpart to this entry point (it is a deployment aid). */
 icwf_status icwf_observables_static(icwf_handle h, icwf_obs* out);
 

@@ -41,7 +41,7 @@ class icwf_info(ct.Structure):
     _fields_ = [("rank", ct.c_int32), ("tail_rel", ct.c_double), ("next_rel", ct.c_double),
                 ("sigma_max", ct.c_double), ("device_bytes", ct.c_size_t),
                 ("steps_done", ct.c_int64), ("t", ct.c_double),
-                ("kernel_launches", ct.c_int64)]
+                ("kernel_launches", ct.c_int64), ("obs_bytes", ct.c_size_t)]
 
 
 class icwf_obs(ct.Structure):

@@ -97,6 +97,7 @@ struct icwf_ctx {
   double *pop = nullptr, *decoh = nullptr;
   double2* proj = nullptr;
   std::vector<void*> extra_allocs;
+  size_t obs_bytes = 0;                     // observables work buffers (allocated on first use)
   // tensor-core assembly scratch
   void* tc_scratch = nullptr;
   size_t tc_scratch_bytes = 0;
@@ -422,6 +423,7 @@ icwf_status alloc_obs(icwf_ctx* h) {
                        align256((size_t)8 * h->nR * sizeof(double2));
   CK(cudaMalloc(&p, bytes));
   h->extra_allocs.push_back(p);
+  h->obs_bytes = bytes;
   Arena a{(char*)p, bytes, 0};
   h->Psi = (double2*)a.take((size_t)h->nx * h->nR * sizeof(double2));
   h->rho_x = (double*)a.take((size_t)(h->nx + h->nR) * sizeof(double));
@@ -993,6 +995,7 @@ icwf_status icwf_get_info(icwf_handle h, icwf_info* out) {
   out->steps_done = h->steps;
   out->t = h->t;
   out->kernel_launches = h->launches;
+  out->obs_bytes = h->obs_bytes;
   return ICWF_OK;
 }
 

@@ -1,19 +1,21 @@
 // icwf_observables_static: the observables of icwf_observables computed without allocating any
 // device memory during the call.
 //
-// Who needs it: callers that cannot call cudaMalloc while they run, e.g. code that is being
-// captured into a CUDA graph (allocation is not capturable), or hosts whose allocator policy
-// forbids device allocation after start-up.  icwf_observables allocates its work buffers (the
-// wavefunction on the full grid and the reduction partials) on its first call; this entry point
-// uses one fixed work area compiled into the library instead.
+// Who needs it: hosts whose allocator policy forbids device allocation once they have started,
+// e.g. an application that reserves its device memory in one arena at start-up and treats any
+// later cudaMalloc as a fault, or a deployment that must not allocate on its serving path.
+// icwf_observables allocates its work buffers (the wavefunction on the full grid and the reduction
+// partials) on its first call; this entry point uses one fixed work area compiled into the library
+// instead.  The call copies its results into the caller's (pageable) host arrays and waits for its
+// stream, so it must run outside any stream capture.
 //
 // The work area is a file-scope static device array of ICWF_OBS_STATIC_BYTES bytes; every GPU
 // that loads the library holds it until the process exits.  Host code cannot use the array's name
 // as a device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; make that first call before any
-// stream capture.  All calls share the one work area: calls that overlap on the GPU race, so the
-// caller serialises them.  Each call writes every part of the work area that it later reads, so
-// nothing carried over from an earlier call needs clearing.
+// cudaGetSymbolAddress (with that device current) and caches it.  All calls share the one work
+// area: calls that overlap on the GPU race, so the caller serialises them.  Each call writes every
+// part of the work area that it later reads, so nothing carried over from an earlier call needs
+// clearing.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -104,6 +106,11 @@ extern "C" icwf_status icwf_observables_static(icwf_handle h, icwf_obs* out) {
   else launch_reconstruct<double>(v.j, v.C, Psi, s);
   launch_obs_lines(v.j, Psi, v.phi, v.n_states, rho_x, rho_R, proj, part, o4, pop, decoh,
                    v.twx_d, v.twR_d, s);
+  // a launch error of these kernels is reported without clearing errors left by other callers
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    handle_set_error(h, "icwf_observables_static: kernel launch failed");
+    return ICWF_ERR_CUDA;
+  }
   double host4[4];
   int cl[2];
   bool ok = cudaMemcpyAsync(host4, o4, sizeof(host4), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
@@ -117,7 +124,7 @@ extern "C" icwf_status icwf_observables_static(icwf_handle h, icwf_obs* out) {
   if (ok && out->decoh && v.n_states)
     ok = cudaMemcpyAsync(out->decoh, decoh, (size_t)v.n_states * v.n_states * 8,
                          cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  if (ok) ok = cudaStreamSynchronize(s) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+  if (ok) ok = cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) {
     handle_set_error(h, "icwf_observables_static: a CUDA call failed");
     return ICWF_ERR_CUDA;

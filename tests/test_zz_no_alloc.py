@@ -1,11 +1,12 @@
 """icwf_observables_static: the allocation-free variant of icwf_observables.
 
-Some callers cannot allocate device memory while they run (code captured into a CUDA graph, or
-an allocator policy that forbids cudaMalloc after start-up).  The variant computes the same
-observables in a fixed work area compiled into the library.  This test calls it through the C ABI
-twice in a row and checks both results against icwf_observables on the same state, and checks
-that a grid larger than the work area is rejected with an argument error.  The file name makes
-pytest collect it last.
+Some hosts forbid device allocation once they have started (an application that reserves its
+device memory in one arena at start-up, or a serving path that must not allocate).  The variant
+computes the same observables in a fixed work area compiled into the library.  These tests call
+it through the C ABI twice in a row and check both results against icwf_observables on the same
+state, check that a fresh handle's first static call leaves the device's free memory and the
+handle's lazily allocated observables buffers untouched, and check that a grid larger than the
+work area is rejected with an argument error.  The file name makes pytest collect it last.
 """
 import numpy as np
 import pytest
@@ -61,4 +62,36 @@ def test_static_observables_reject_grids_beyond_the_work_area():
     with pytest.raises(g.IcwfError) as e:
         g.icwf_observables_static(sim.h, nx, nR)
     assert e.value.status == g.ICWF_ERR_ARG and "too large" in str(e.value)
+    sim.close()
+
+
+def test_static_observables_allocate_no_device_memory():
+    """On a grid near the limit (1024 x 512: the allocating call would take about 9 MiB for the
+    wavefunction on the grid), a fresh handle's first static call changes neither the device's
+    free memory nor the handle's observables buffers (still unallocated)."""
+    torch = pytest.importorskip("torch")
+    small = shin_metiu(n_traj=4, svd_rel_cutoff=1e-8)
+    warm = g.Icwf(g.params_from(small, precision=0), small.V)
+    warm.init_from_density(small.psi0, 0)
+    # the library's static work area is reserved when its device code is first loaded in this
+    # process; one call on another handle makes sure that has happened before the measurement
+    g.icwf_observables_static(warm.h, small.nx, small.nR)
+    warm.close()
+    w = shin_metiu(nx=1024, x_range=(-100.0, 100.0), nR=512, R_range=(-9.5, 9.5), n_traj=16,
+                   dt=0.05, svd_rel_cutoff=1e-8)
+    sim = g.Icwf(g.params_from(w, precision=0), w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, 0)
+    sim.step(2)
+    assert sim.info()["obs_bytes"] == 0
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    first = g.icwf_observables_static(sim.h, w.nx, w.nR)
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    assert free_before - free_after < 2 * 1024 * 1024
+    assert sim.info()["obs_bytes"] == 0
+    ref = sim.observables()                     # the allocating entry point, for comparison
+    assert sim.info()["obs_bytes"] >= w.nx * w.nR * 16
+    _close(first, ref)
     sim.close()
