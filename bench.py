@@ -74,15 +74,24 @@ def parse():
     ap.add_argument("--serving-jobs", type=int, default=24,
                     help="jobs in the serving stream measured beside the throughput (0: skip)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode comparison run")
+    ap.add_argument("--workload", default="shin_metiu", choices=["shin_metiu", "cavity"],
+                    help="Shin-Metiu 1024 x 512 (default) or the cavity 2048 x 256")
+    ap.add_argument("--lam", type=float, default=0.5, help="cavity coupling lambda")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the rank-error, mixed-vs-FP64 and cavity reports")
     return ap.parse_args()
 
 
-def make_workload(n_traj, cutoff, eps, nx=1024, nR=512):
+def make_workload(n_traj, cutoff, eps, nx=1024, nR=512, kind="shin_metiu", lam=0.5):
     from workloads import WORKLOADS
+    if kind == "cavity":
+        return WORKLOADS["cavity"](n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps, lam=lam)
     return WORKLOADS["sm_paper"](n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps, nx=nx, nR=nR)
 
 
 def workload_name(w):
+    if w.model.get("kind") == "cavity":
+        return f"cavity_{w.nx}x{w.nR}_lambda{w.model['lam']}_N{w.n_traj}_dt{w.dt}"
     return f"shin_metiu_{w.nx}x{w.nR}_N{w.n_traj}_dt{w.dt}"
 
 
@@ -243,40 +252,40 @@ def roofline(prof, w, K, mode, peaks, solve="df64", nfact=2):
 
 # ---------------------------------------------------------------- our arm
 
-def run_ours(args, rank, ws, local):
-    import numpy as np
+def n_obs_calls(steps):
+    """Observables calls in a timed region of `steps` steps: one every OBS_EVERY steps, and at
+    least one, so that a short timed region still pays for them (never fewer than the metric's
+    rate of one per 100 steps)."""
+    return max(1, steps // OBS_EVERY)
+
+
+def timed_steps(sim, steps, warmup, local, ws=1):
+    """W untimed steps, then `steps` steps timed one by one with CUDA events on the library's
+    stream (L2 flushed before each), observables n_obs_calls(steps) times inside the timed
+    region; per-family kernel times from the library's own events; clocks sampled meanwhile."""
     import torch
     import paper_1805_11169_gb300 as g
-
-    torch.cuda.set_device(local)
-    prec, dtype_name, cutoff, eps = MODES[args.mode]
-    w = make_workload(args.n_traj, cutoff, eps, args.nx, args.nR)
-    params = g.params_from(w, precision=prec, solve_fp64=int(args.solve == "fp64"),
-                           coeff_scheme=int(args.coeff_scheme == "frozen"))
-
-    sim = g.Icwf(params, w.V)
-    sim.set_projectors(w.phi)
-    sim.init_from_density(w.psi0, w.seed)
-    info = sim.info()
     stream = torch.cuda.ExternalStream(sim.stream())
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         sim.step(1)
     g.icwf_profile_reset(sim.h)
     g.icwf_profile_enable(sim.h, True)
     launches0 = sim.info()["kernel_launches"]
+    n_obs = n_obs_calls(steps)
+    obs_at = {steps - 1 - k * (steps // n_obs) for k in range(n_obs)}
     barrier(ws)
     torch.cuda.synchronize()
     step_ms = []
     with Clocks(local) as clk:
-        for s in range(args.steps):
+        for s in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             sim.step(1)
-            if (s + 1) % OBS_EVERY == 0:
+            if s in obs_at:
                 sim.observables()
             e1.record(stream)
             e1.synchronize()
@@ -285,18 +294,38 @@ def run_ours(args, rank, ws, local):
     barrier(ws)
     g.icwf_profile_enable(sim.h, False)
     prof = g.icwf_profile_read(sim.h)
-    launches = sim.info()["kernel_launches"] - launches0
-    n_obs = args.steps // OBS_EVERY
-    obs_launches = 4 * n_obs
-    total_s = max_over_ranks(sum(step_ms) / 1e3, ws)
+    launches = sim.info()["kernel_launches"] - launches0 + 4 * n_obs
+    return sum(step_ms), prof, launches, clk.summary(), n_obs
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_ours(args, rank, ws, local):
+    import numpy as np
+    import torch
+    import paper_1805_11169_gb300 as g
+
+    torch.cuda.set_device(local)
+    prec, dtype_name, cutoff, eps = MODES[args.mode]
+    w = make_workload(args.n_traj, cutoff, eps, args.nx, args.nR, args.workload, args.lam)
+    params = g.params_from(w, precision=prec, solve_fp64=int(args.solve == "fp64"),
+                           coeff_scheme=int(args.coeff_scheme == "frozen"))
+
+    sim = g.Icwf(params, w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, w.seed)
+    info = sim.info()
+    total_ms, prof, launches, clocks, n_obs = timed_steps(sim, args.steps, args.warmup, local, ws)
+    total_s = max_over_ranks(total_ms / 1e3, ws)
     value = whole_job_rate(ws, w.n_traj * args.steps, total_s)
     sim.close()
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+    peaks, _ = load_peaks()
     prof_step = {f: v for f, v in prof.items() if v[1] > 0 and f != "observables"}
     rl = roofline(prof_step, w, info["rank"], args.mode, peaks, args.solve,
                   1 if args.coeff_scheme == "frozen" else 2)
@@ -313,24 +342,31 @@ def run_ours(args, rank, ws, local):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": dtype_name,
-        "data": "synthetic (Shin-Metiu potential, BO states and |Psi0|^2 sampling computed here)",
+        "data": ("synthetic (%s potential, BO states and |Psi0|^2 sampling computed here)"
+                 % ("cavity" if args.workload == "cavity" else "Shin-Metiu")),
         "config": {"workload": workload_name(w), "nx": w.nx, "nR": w.nR, "n_traj": w.n_traj,
                    "dt": w.dt, "rank_k": info["rank"], "svd_rel_cutoff": cutoff, "s_reg_eps": eps,
                    "svd_tail_rel": info["tail_rel"], "coeff_scheme": "rk4-" + args.coeff_scheme,
                    "solve": ("fp64" if args.mode == "fp64" or args.solve == "fp64"
                              else "double-float (FP32 pairs)"),
-                   "obs_every": OBS_EVERY, "l2": "flushed (256 MB write) before every timed step",
+                   "obs_every": OBS_EVERY, "obs_calls_timed": n_obs,
+                   "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": rl,
         "kernels_ms_per_step": {f: v[0] / args.steps for f, v in prof.items() if v[1]},
-        "gpu_launches": int(launches + obs_launches),
-        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+        "clocks": clocks,
     }
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, w, params, g)
     if rank == 0 and not args.no_fp64 and args.mode != "fp64":
         out["fp64"] = run_fp64_comparison()
         out["speedup_vs_fp64"] = value / out["fp64"]["value"]
+    if rank == 0 and not args.no_extras and args.workload == "shin_metiu":
+        out["rank_error"] = run_rank_error(args.mode)
+        if args.mode != "fp64":
+            out["mixed_vs_fp64"] = run_mixed_vs_fp64(args.mode, eps)
+        out["cavity"] = run_cavity_line(args, local, peaks)
     if rank == 0 and not args.no_exact2d:
         out["exact2d"] = run_exact2d(w)
     if rank == 0 and args.vs_exact > 0:
@@ -478,6 +514,82 @@ def run_fp64_comparison(steps=10, warmup=2):
     return {"value": w.n_traj * steps / (ms / 1e3), "unit": "trajectory-steps/s",
             "ms_per_step": ms / steps, "dtype": dtype_name, "rank_k": k, "steps": steps,
             "svd_rel_cutoff": cutoff, "s_reg_eps": eps}
+
+
+def run_rank_error(mode, steps=10, n_cols=16):
+    """Error of the factorised Heff (rank k from the SVD cutoff) against the full
+    O(N^2 nx nR) contraction, on sampled columns at the bench configuration (N = 1024,
+    1024 x 512, after `steps` steps): the full double sum comes from icwf_heff_direct (FP64,
+    same CWFs and positions).  Reported for the FP64 mode at cutoffs 1e-8 and 1e-12 (rank
+    truncation alone) and for the mixed mode at its cutoff (truncation + tensor-core rounding)."""
+    import numpy as np
+    import paper_1805_11169_gb300 as g
+    rng = np.random.default_rng(7)
+    cols = np.sort(rng.choice(1024, n_cols, replace=False)).astype(np.int32)
+    out = {"n_cols": n_cols, "steps": steps, "metric": "max over sampled columns b of "
+           "||Heff_factorised[:, b] - Heff_direct[:, b]|| / ||Heff_direct[:, b]||"}
+    runs = [("fp64", 0, 1e-8), ("fp64", 0, 1e-12)]
+    if mode != "fp64":
+        runs.append((mode, MODES[mode][0], MODES[mode][2]))
+    for name, prec, cutoff in runs:
+        w = make_workload(1024, cutoff, MODES[name][3])
+        sim = g.Icwf(g.params_from(w, precision=prec), w.V)
+        sim.init_from_density(w.psi0, w.seed)
+        sim.step(steps)
+        Hd = sim.heff_direct(cols)
+        Hf = sim.matrices()["Heff"][:, cols]
+        errs = np.linalg.norm(Hf - Hd, axis=0) / np.linalg.norm(Hd, axis=0)
+        info = sim.info()
+        out[f"{name}_cutoff{cutoff:g}"] = {"rank_k": info["rank"], "svd_tail_rel": info["tail_rel"],
+                                           "max_rel": float(errs.max()),
+                                           "median_rel": float(np.median(errs))}
+        sim.close()
+    return out
+
+
+def run_mixed_vs_fp64(mode, eps_mixed, steps=100):
+    """Mixed mode at its own eps against the FP64 mode at eps 1e-6 (both on the GPU, same
+    N = 1024 job, same seed) after `steps` steps: L1 distances of rho_x, rho_R and the BO
+    populations, and the norms."""
+    import numpy as np
+    import paper_1805_11169_gb300 as g
+    res = {}
+    for name in ("fp64", mode):
+        prec, _, cutoff, eps = MODES[name]
+        w = make_workload(1024, cutoff, eps)
+        sim = g.Icwf(g.params_from(w, precision=prec), w.V)
+        sim.set_projectors(w.phi)
+        sim.init_from_density(w.psi0, w.seed)
+        sim.step(steps)
+        res[name] = sim.observables()
+        sim.close()
+    a, b = res[mode], res["fp64"]
+    return {"steps": steps, "mixed_eps": eps_mixed, "fp64_eps": MODES["fp64"][3],
+            "rho_x_L1": float(w.dx * np.sum(np.abs(a["rho_x"] - b["rho_x"]))),
+            "rho_R_L1": float(w.dR * np.sum(np.abs(a["rho_R"] - b["rho_R"]))),
+            "pop_L1": float(np.sum(np.abs(a["pop"] - b["pop"]))),
+            "norm_mixed": float(a["norm"]), "norm_fp64": float(b["norm"])}
+
+
+def run_cavity_line(args, local, peaks, steps=50, warmup=3):
+    """Throughput of the same mode on the cavity workload (2048 x 256, lambda 0.5, N = 1024,
+    dt = 0.05; V_c exactly rank 1), timed like the headline, with its own roofline entry."""
+    import paper_1805_11169_gb300 as g
+    prec, _, cutoff, eps = MODES[args.mode]
+    w = make_workload(1024, cutoff, eps, kind="cavity", lam=args.lam)
+    sim = g.Icwf(g.params_from(w, precision=prec), w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, w.seed)
+    k = sim.info()["rank"]
+    total_ms, prof, launches, clocks, n_obs = timed_steps(sim, steps, warmup, local)
+    sim.close()
+    prof_step = {f: v for f, v in prof.items() if v[1] > 0 and f != "observables"}
+    return {"workload": workload_name(w), "value": w.n_traj * steps / (total_ms / 1e3),
+            "unit": "trajectory-steps/s", "ms_per_step": total_ms / steps, "steps": steps,
+            "rank_k": k, "obs_calls_timed": n_obs, "gpu_launches": int(launches),
+            "roofline": roofline(prof_step, w, k, args.mode, peaks, args.solve),
+            "kernels_ms_per_step": {f: v[0] / steps for f, v in prof.items() if v[1]},
+            "clocks": clocks}
 
 
 def _model_library(rng):

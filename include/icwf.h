@@ -161,6 +161,33 @@ icwf_status icwf_get_matrices(icwf_handle h, double* S, double* H, double* Heff)
 
 icwf_status icwf_get_info(icwf_handle h, icwf_info* out);
 
+/* Columns of Heff = W - W1 - W2 (Eq. W, W1, W2) by the full double sum over the grid, without the
+ * rank-k factorisation of V:
+ *   Heff[a, b] = dx dR sum_ij conj(psi_a(x_i) chi_a(R_j)) [V(x_i,R_j) - V(x_i,R_b) - V(x_b,R_j)]
+ *                psi_b(x_i) chi_b(R_j),
+ * on the handle's current CWFs and positions, in FP64 arithmetic (the CWFs are read in their
+ * storage precision), O(N nx nR) work per column.  It is the reference the factorised assembly's
+ * error is reported against (the paper flags this contraction as the costly part of the method
+ * for large ensembles).  cols[m] in [0, N) for m < n_cols (1 <= n_cols <= N);
+ * out[2*(m*N + a) + {0,1}] = Heff[a, cols[m]] (complex128, host, caller-owned).  Allocates and
+ * frees its own device work buffer (about 16 N n_cols (nx/64 + 1) bytes). */
+icwf_status icwf_heff_direct(icwf_handle h, int32_t n_cols, const int32_t* cols, double* out);
+
+/* Change the Tikhonov shift eps of the solves (S + eps I) for the following steps.  Any finite
+ * value is accepted; a negative eps makes S + eps I indefinite, so the next step's Cholesky
+ * fails and returns ICWF_ERR_NUMERIC (the failure path the tests drive on purpose). */
+icwf_status icwf_set_regularisation(icwf_handle h, double eps);
+
+/* Diagnostic: poll budget of the in-kernel spin waits on global flags (the look-ahead tickets of
+ * the blocked Cholesky factorisation and the block flags of the triangular solves).  polls >= 0:
+ * such a wait gives up after that many polls, sets the timeout flag and the kernel continues
+ * without its input (results are then meaningless and the call returns ICWF_ERR_TIMEOUT);
+ * polls < 0 restores the compiled-in limits (well under a second of polling).  Waits on
+ * shared-memory barriers that guard asynchronous copies (the tensor-core assembly, the cluster
+ * triangular solve) always keep their 2-second limit, so that no copy can land after its kernel
+ * has released its memory.  icwf_init_* reset the budget to the defaults. */
+icwf_status icwf_set_wait_limit(icwf_handle h, int64_t polls);
+
 /* The handle's CUDA stream (a cudaStream_t) for callers that record events on it. */
 icwf_status icwf_get_stream(icwf_handle h, void** stream);
 

@@ -71,7 +71,10 @@ def _load():
         "icwf_get_state": [H, d, d, d, d, d],
         "icwf_get_matrices": [H, d, d, d],
         "icwf_get_info": [H, P(icwf_info)],
+        "icwf_heff_direct": [H, ct.c_int32, P(ct.c_int32), d],
         "icwf_get_stream": [H, P(ct.c_void_p)],
+        "icwf_set_regularisation": [H, ct.c_double],
+        "icwf_set_wait_limit": [H, ct.c_int64],
         "icwf_profile_enable": [H, ct.c_int32],
         "icwf_profile_reset": [H],
         "icwf_profile_read": [H, ct.c_int32, P(ct.c_char_p), d, P(ct.c_int64), P(ct.c_int32)],
@@ -217,6 +220,23 @@ def icwf_get_info(h) -> dict:
     return {k: getattr(i, k) for k, _ in icwf_info._fields_}
 
 
+def icwf_set_regularisation(h, eps: float):
+    _check(LIB.icwf_set_regularisation(h, ct.c_double(eps)), h)
+
+
+def icwf_set_wait_limit(h, polls: int):
+    _check(LIB.icwf_set_wait_limit(h, ct.c_int64(polls)), h)
+
+
+def icwf_heff_direct(h, N: int, cols) -> np.ndarray:
+    """Heff[:, cols] by the full double sum over the grid (N x len(cols) complex128)."""
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    out = np.zeros((len(cols), N), dtype=np.complex128)
+    _check(LIB.icwf_heff_direct(h, len(cols), cols.ctypes.data_as(ct.POINTER(ct.c_int32)),
+                                out.ctypes.data_as(ct.POINTER(ct.c_double))), h)
+    return out.T.copy()
+
+
 def icwf_get_stream(h) -> int:
     s = ct.c_void_p()
     _check(LIB.icwf_get_stream(h, ct.byref(s)), h)
@@ -338,8 +358,17 @@ class Icwf:
     def info(self):
         return icwf_get_info(self.h)
 
+    def heff_direct(self, cols):
+        return icwf_heff_direct(self.h, self.p.n_traj, cols)
+
     def stream(self):
         return icwf_get_stream(self.h)
+
+    def set_regularisation(self, eps):
+        icwf_set_regularisation(self.h, eps)
+
+    def set_wait_limit(self, polls):
+        icwf_set_wait_limit(self.h, polls)
 
     def release(self):
         """Give up ownership (after icwf_pool_submit the pool owns the handle)."""

@@ -999,6 +999,22 @@ icwf_status icwf_get_info(icwf_handle h, icwf_info* out) {
   return ICWF_OK;
 }
 
+icwf_status icwf_set_regularisation(icwf_handle h, double eps) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_set_regularisation: NULL handle");
+  if (!std::isfinite(eps)) return fail(h, ICWF_ERR_ARG, "icwf_set_regularisation: eps is not finite");
+  h->p.s_reg_eps = eps;
+  return ICWF_OK;
+}
+
+icwf_status icwf_set_wait_limit(icwf_handle h, int64_t polls) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_set_wait_limit: NULL handle");
+  if (polls > (int64_t)INT32_MAX - 1) return fail(h, ICWF_ERR_ARG, "icwf_set_wait_limit: polls too large");
+  const int v = polls < 0 ? 0 : (int)polls + 1;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(h->status + STATUS_WAITLIM, &v, sizeof(int), cudaMemcpyHostToDevice));
+  return ICWF_OK;
+}
+
 icwf_status icwf_get_stream(icwf_handle h, void** stream) {
   if (!h || !stream) return fail(h, ICWF_ERR_ARG, "icwf_get_stream: NULL argument");
   *stream = (void*)h->stream;

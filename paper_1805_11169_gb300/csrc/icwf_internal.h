@@ -18,7 +18,10 @@ enum : int {
   ST_TIMEOUT = 4,       // bounded wait gave up
   ST_ARG = 8            // kernel saw an out-of-range size
 };
-enum : int { STATUS_FLAGS = 0, STATUS_CLAMPED = 1, STATUS_TICKET = 2, STATUS_WORDS = 8 };
+// STATUS_WAITLIM: 0 = the compiled-in limits of the spin waits on global flags; k > 0 = those waits
+// give up after k - 1 polls (set by icwf_set_wait_limit, a diagnostic for the timeout path).
+enum : int { STATUS_FLAGS = 0, STATUS_CLAMPED = 1, STATUS_TICKET = 2, STATUS_WAITLIM = 3,
+             STATUS_WORDS = 8 };
 
 // ---------------------------------------------------------------- launch descriptors
 

@@ -111,6 +111,13 @@ __device__ __forceinline__ void ifft_dit(Z* buf, const Z* __restrict__ tw, int n
 
 __device__ __forceinline__ void set_flag(int* status, int bit) { atomicOr(status + STATUS_FLAGS, bit); }
 
+// Poll budget of a spin wait on a global flag: the compiled-in default, or the handle's override
+// (status word STATUS_WAITLIM, see icwf_set_wait_limit).
+__device__ __forceinline__ unsigned wait_budget(const int* status, unsigned dflt) {
+  const int v = *((const volatile int*)status + STATUS_WAITLIM);
+  return v > 0 ? (unsigned)(v - 1) : dflt;
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

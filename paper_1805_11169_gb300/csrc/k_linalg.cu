@@ -329,7 +329,8 @@ void launch_matvec(int N, const double2* H0, const double2* H1, double theta, co
 // ------------------------------------------------------------------------------ triangular solves
 
 __device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned epoch, int* status) {
-  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+  const unsigned lim = wait_budget(status, WAIT_LIMIT);
+  for (unsigned it = 0; it < lim; ++it) {
     if (ld_acquire(f) == epoch) return true;
     if (it > 4096) __nanosleep(64);   // pure spin first: the expected wait is a few microseconds
   }

@@ -178,7 +178,8 @@ __device__ __forceinline__ cdf kara_val(acc2 p1, acc2 p2, acc2 p3) {
 }
 
 __device__ __forceinline__ bool cs_wait(const unsigned* f, unsigned target, int* status) {
-  for (unsigned it = 0; it < CS_WAIT_LIMIT; ++it) {
+  const unsigned lim = wait_budget(status, CS_WAIT_LIMIT);
+  for (unsigned it = 0; it < lim; ++it) {
     if (ld_acquire(f) >= target) return true;
     if (it > 256) __nanosleep(128);
   }
@@ -567,7 +568,8 @@ constexpr int CW = 4;
 constexpr int CPW = NB / CW;
 
 __device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned epoch, int* status) {
-  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+  const unsigned lim = wait_budget(status, WAIT_LIMIT);
+  for (unsigned it = 0; it < lim; ++it) {
     if (ld_acquire(f) == epoch) return true;
     if (it > 4096) __nanosleep(64);
   }
