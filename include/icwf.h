@@ -62,7 +62,8 @@ typedef enum {
 } icwf_precision;
 
 typedef struct {
-  int32_t nx, nR;           /* grid sizes; powers of two in [8, 4096] (radix-2 FFT) */
+  int32_t nx, nR;           /* grid sizes; powers of two in [8, 4096] (radix-2 FFT); the mixed
+                               modes need nx, nR >= 64 */
   double x_min, x_max;      /* electron grid extent (periodic cell) */
   double R_min, R_max;      /* nuclear / photon grid extent */
   double mass_x, mass_R;    /* masses in atomic units (e.g. 1 and 1836, or 1 and 1) */
@@ -77,6 +78,12 @@ typedef struct {
   int32_t solve_fp64;       /* mixed modes only: 1 runs the Cholesky factorisations and triangular
                                solves in FP64 (as ICWF_FP64 does) instead of double-float;
                                ignored by ICWF_FP64 */
+  int32_t overlap_split;    /* mixed modes only: 0 (default) computes S = S1 o S2 as exact Grams
+                               of the CWFs in a 4-digit fixed-point form on the tensor cores, so
+                               S is positive semidefinite to FP64 rounding and eps can be as
+                               small as in ICWF_FP64; 1 takes S from the same split products
+                               with FP32 accumulation as the other Grams (rounding ~1e-6 of S,
+                               whose indefinite part needs eps ~1e-3 at N = 1024) */
 } icwf_params;
 
 /* Diagnostic facts about a handle. */

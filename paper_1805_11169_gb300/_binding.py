@@ -34,7 +34,7 @@ class icwf_params(ct.Structure):
                 ("dt", ct.c_double), ("n_traj", ct.c_int32), ("precision", ct.c_int32),
                 ("svd_rel_cutoff", ct.c_double), ("s_reg_eps", ct.c_double),
                 ("coeff_scheme", ct.c_int32), ("max_rank", ct.c_int32),
-                ("solve_fp64", ct.c_int32)]
+                ("solve_fp64", ct.c_int32), ("overlap_split", ct.c_int32)]
 
 
 class icwf_info(ct.Structure):
@@ -311,7 +311,7 @@ def params_from(w, precision: int = ICWF_FP64, coeff_scheme: int = 0, **over) ->
     d = dict(nx=w.nx, nR=w.nR, x_min=w.x_min, x_max=w.x_max, R_min=w.R_min, R_max=w.R_max,
              mass_x=w.mass_x, mass_R=w.mass_R, dt=w.dt, n_traj=w.n_traj, precision=precision,
              svd_rel_cutoff=w.svd_rel_cutoff, s_reg_eps=w.s_reg_eps, coeff_scheme=coeff_scheme,
-             max_rank=0, solve_fp64=0)
+             max_rank=0, solve_fp64=0, overlap_split=0)
     d.update(over)
     return icwf_params(**d)
 

@@ -325,7 +325,8 @@ void assemble(icwf_ctx* h, double2* S, double2* Hm) {
   h->launches += h->mixed ? 3 : 1;   // operand planes (two sides) + Grams, or the FP64 kernel
   JobView j = view(h);
   if (h->mixed) {
-    launch_assemble_tc(j, h->p.precision, S, Hm, h->tc_scratch, h->tc_scratch_bytes, h->stream);
+    launch_assemble_tc(j, h->p.precision, h->p.overlap_split == 0, S, Hm, h->tc_scratch,
+                       h->tc_scratch_bytes, h->stream);
   } else {
     launch_assemble_fp64(j, S, Hm, h->stream);
   }
@@ -489,6 +490,10 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
     return fail(nullptr, ICWF_ERR_ARG, "icwf_create: mixed precision is not available in this library");
   if (p.coeff_scheme < 0 || p.coeff_scheme > 1)
     return fail(nullptr, ICWF_ERR_ARG, "icwf_create: unknown coeff_scheme");
+  if (p.precision != ICWF_FP64 && (p.nx < 64 || p.nR < 64))
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: mixed precision needs nx, nR >= 64");
+  if (p.overlap_split < 0 || p.overlap_split > 1)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_create: overlap_split must be 0 or 1");
   const size_t nV = (size_t)p.nx * p.nR;
   for (size_t e = 0; e < nV; ++e)
     if (!std::isfinite(Vh[e])) return fail(nullptr, ICWF_ERR_ARG, "icwf_create: V has a non-finite entry");

@@ -159,8 +159,13 @@ bool handle_obs_view(icwf_handle h, ObsView* v);
 void handle_set_error(icwf_handle h, const char* msg);
 
 // Mixed-precision assembly on the tensor cores (tcgen05); returns false if unsupported sizes.
-bool launch_assemble_tc(const JobView& j, int kind, double2* S, double2* H, void* scratch,
-                        size_t scratch_bytes, cudaStream_t s);
+// exact_s: S from launch_gram_s (exact Grams of fixed-point CWFs), else from the split products.
+bool launch_assemble_tc(const JobView& j, int kind, bool exact_s, double2* S, double2* H,
+                        void* scratch, size_t scratch_bytes, cudaStream_t s);
 size_t assemble_tc_scratch_bytes(int N, int nx, int nR, int K);
+// S = S1 o S2 as exact Grams of 4-digit fixed-point complex64 CWFs on the tensor cores
+// (k_gram_s.cu); scratch of gram_s_scratch_bytes.  Returns false if it does not fit.
+bool launch_gram_s(const JobView& j, double2* S, void* scratch, size_t bytes, cudaStream_t s);
+size_t gram_s_scratch_bytes(int N, int nx, int nR);
 
 }  // namespace icwf

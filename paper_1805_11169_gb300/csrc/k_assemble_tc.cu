@@ -28,6 +28,7 @@
 
 #include "icwf_internal.h"
 #include "k_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace icwf {
 
@@ -48,7 +49,6 @@ constexpr int TMEM_COLS = 512;
 constexpr int COL_ACC = 0;       // [0, 256): g accumulators, side-major
 constexpr int COL_S = 256;       // [256, 384): S1 (re, im) for 32 kets, then S2 (re, im)
 constexpr int COL_H = 384;       // [384, 512): Heff (re, im) and the mirrored entries (re, im)
-constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 struct Args {
   int N, nx, nR, K;
@@ -63,138 +63,19 @@ struct Args {
   int kind;           // 0 bf16, 1 tf32
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long gtime() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; returns false (and raises the abort flag) on timeout or if another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag,
-                                         int* status) {
-  const unsigned long long t0 = gtime();
-  while (true) {
-    if (mbar_test(b, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtime() - t0 > WAIT_NS) {
-      *abort_flag = 1;
-      set_flag(status, ST_TIMEOUT);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading-dimension offset (unused with this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride between 8-row groups
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: D = F32, A = B = BF16 (kind 0) or TF32 (kind 1), both K-major,
-// M = 128, N = 64 (the P and Q planes of 32 kets side by side).
+// Instruction descriptor of this kernel's MMAs: M = 128, N = 64 (the P and Q planes of 32 kets
+// side by side).
 constexpr int BN_MMA = 2 * BNT;
-__host__ __device__ constexpr uint32_t idesc(int kind) {
-  return (1u << 4) | ((kind ? 2u : 1u) << 7) | ((kind ? 2u : 1u) << 10) |
-         ((uint32_t)(BN_MMA >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
+__host__ __device__ constexpr uint32_t idesc(int kind) { return idesc_mn(kind, BM, BN_MMA); }
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  if (KIND == 0) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc(0)), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
-  }
+  mma_desc<KIND>(d_tmem, a, b, idesc(KIND), acc);
 }
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// 8 consecutive 32-bit TMEM columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 struct Maps {
   CUtensorMap xhi_a, xlo_a, Rhi_a, Rlo_a;   // 128-row boxes (bra planes)
   CUtensorMap xhi_b, xlo_b, Rhi_b, Rlo_b;   // 32-row boxes (ket planes)
 };
-
-// Block (I <= J) of 128 x 128 trajectories and ket quarter q from the linear CTA index.
-__device__ __forceinline__ void block_index(int t, int& I, int& J, int& q) {
-  q = t & 3;
-  t >>= 2;
-  int Jc = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while (Jc * (Jc + 1) / 2 > t) --Jc;
-  while ((Jc + 1) * (Jc + 2) / 2 <= t) ++Jc;
-  J = Jc;
-  I = t - Jc * (Jc + 1) / 2;
-}
 
 template <int KIND>
 __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_constant__ Maps maps) {
@@ -449,10 +330,10 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
           const double sr = (double)s1r[e] * s2r[e] - (double)s1i[e] * s2i[e];
           const double si = (double)s1r[e] * s2i[e] + (double)s1i[e] * s2r[e];
           const double db = args.d[b];
-          args.S[(size_t)a * N + b] = make_double2(sr, si);
+          if (args.S) args.S[(size_t)a * N + b] = make_double2(sr, si);
           args.H[(size_t)a * N + b] = make_double2(hr[e] - db * sr, hi[e] - db * si);
           if (mirror) {
-            args.S[(size_t)b * N + a] = make_double2(sr, -si);
+            if (args.S) args.S[(size_t)b * N + a] = make_double2(sr, -si);
             args.H[(size_t)b * N + a] = make_double2(tr[e] - da * sr, ti[e] + da * si);
           }
         }
@@ -534,19 +415,6 @@ __global__ void k_prep(const float2* __restrict__ cwf, const double* __restrict_
 
 // ---------------------------------------------------------------------------- host side
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, []() {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  });
-  return fn;
-}
-
 bool make_map(CUtensorMap* m, void* base, int kind, int n, size_t rows, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -564,15 +432,19 @@ bool make_map(CUtensorMap* m, void* base, int kind, int n, size_t rows, int box_
 
 }  // namespace tc
 
-bool launch_assemble_tc(const JobView& j, int precision, double2* S, double2* H, void* scratch,
-                        size_t scratch_bytes, cudaStream_t s) {
+bool launch_assemble_tc(const JobView& j, int precision, bool exact_s, double2* S, double2* H,
+                        void* scratch, size_t scratch_bytes, cudaStream_t s) {
   using namespace tc;
   const int kind = precision == ICWF_MIXED_TF32X3 ? 1 : 0;
   const size_t esz = kind ? 4 : 2;
   const int G = j.K + 1;
   const size_t rx = (size_t)2 * G * j.N, nxe = rx * j.nx * esz, nRe = rx * j.nR * esz;
   auto al = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
-  if (2 * al(nxe) + 2 * al(nRe) > scratch_bytes) return false;
+  const size_t split_bytes = 2 * al(nxe) + 2 * al(nRe);
+  if (split_bytes > scratch_bytes) return false;
+  if (exact_s &&
+      !launch_gram_s(j, S, (char*)scratch + split_bytes, scratch_bytes - split_bytes, s))
+    return false;
   char* p = (char*)scratch;
   void* xhi = p; p += al(nxe);
   void* xlo = p; p += al(nxe);
@@ -598,7 +470,8 @@ bool launch_assemble_tc(const JobView& j, int precision, double2* S, double2* H,
   a.N = j.N; a.nx = j.nx; a.nR = j.nR; a.K = j.K;
   a.dx = (float)j.dx; a.dR = (float)j.dR;
   a.sig = j.sig; a.px = j.px; a.pR = j.pR; a.d = j.d;
-  a.S = S; a.H = H; a.status = j.status; a.kind = kind;
+  a.S = exact_s ? nullptr : S;   // with the exact overlap kernel, S comes from there
+  a.H = H; a.status = j.status; a.kind = kind;
   const int T = (j.N + BM - 1) / BM;
   const unsigned grid = (unsigned)(4 * T * (T + 1) / 2);
   if (kind) {
@@ -612,9 +485,10 @@ bool launch_assemble_tc(const JobView& j, int precision, double2* S, double2* H,
 }
 
 size_t assemble_tc_scratch_bytes(int N, int nx, int nR, int K) {
-  // hi + lo planes (P and Q rows for every Gram) for both sides, TF32 (4 bytes) as the larger
+  // hi + lo planes (P and Q rows for every Gram) for both sides, TF32 (4 bytes) as the larger,
+  // then the digit planes of the exact overlap kernel
   const size_t G = (size_t)K + 1;
-  return 2 * 4 * G * 2 * (size_t)N * ((size_t)nx + nR) + 4 * 1024;
+  return 2 * 4 * G * 2 * (size_t)N * ((size_t)nx + nR) + 4 * 1024 + gram_s_scratch_bytes(N, nx, nR);
 }
 
 }  // namespace icwf

@@ -21,7 +21,7 @@ def oracle_for(w):
                          w.n_traj, w.svd_rel_cutoff, w.s_reg_eps), w.V)
 
 
-@pytest.mark.parametrize("precision,N,nx,nR", [(0, 16, 128, 64), (2, 37, 64, 32), (0, 70, 16, 8),
+@pytest.mark.parametrize("precision,N,nx,nR", [(0, 16, 128, 64), (2, 37, 64, 64), (0, 70, 16, 8),
                                                (1, 5, 256, 64)])
 def test_direct_columns_match_the_oracle_double_sum(precision, N, nx, nR):
     w = shin_metiu(nx=nx, x_range=(-30.0, 30.0), nR=nR, R_range=(-7.0, 7.0), n_traj=N, dt=0.1,
@@ -35,10 +35,15 @@ def test_direct_columns_match_the_oracle_double_sum(precision, N, nx, nR):
     o = oracle_for(w)
     Ho = o.heff_direct(st["psi"], st["chi"], st["x"], st["R"])[:, cols]
     assert np.linalg.norm(Hd - Ho) < 1e-12 * np.linalg.norm(Ho)
-    # the factorised Heff of the step carries the truncation of the kept rank (cutoff 1e-4)
+    # the factorised Heff of the step carries the truncation of the kept rank (cutoff 1e-4);
+    # a grid whose dropped singular values vanish (double-centring leaves V_c rank-deficient)
+    # is factorised exactly
     Hf = sim.matrices()["Heff"][:, cols]
     err = np.linalg.norm(Hf - Hd) / np.linalg.norm(Hd)
-    assert 1e-9 < err < 1e-2, err
+    if sim.info()["tail_rel"] > 1e-8:       # something of size was dropped
+        assert 1e-9 < err < 1e-2, err
+    else:
+        assert err < (1e-12 if precision == 0 else 1e-5), err
     sim.close()
 
 

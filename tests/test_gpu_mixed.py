@@ -1,9 +1,10 @@
 """Mixed-precision path (complex64 CWFs, FP32 propagation, tensor-core Grams as split BF16 or TF32
 products with FP32 accumulation; FP64 solve) against the FP64 oracle.
 
-The tensor cores accumulate in FP32, which leaves rounding noise of about 1e-6 relative in S;
-its spectral norm exceeds the FP64 default regulariser (1e-6), so the mixed modes run with
-eps = 1e-4 (above that noise floor), and the FP64 oracle they are compared with uses the same eps.
+These tests run the mixed modes and the FP64 oracle they are compared with at the same
+eps = 1e-4.  The overlap S itself is an exact Gram of fixed-point CWFs (positive semidefinite; see
+test_gpu_exact_overlap.py, which also compares the mixed modes at the FP64 default eps = 1e-6);
+the other Grams keep about 1e-6 relative FP32 rounding.
 
 Bars:
 * per step, S and Heff within 1e-5 relative Frobenius of the FP64 formulas evaluated on the
