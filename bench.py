@@ -27,11 +27,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 OBS_EVERY = 100
-# mode -> (precision enum, dtype label, SVD cutoff, regulariser eps)
-# mixed modes: eps = 1e-3; with 1e-4 the split-precision rounding of S at N = 1024 exceeds eps
-# in norm after ~650 steps (Cholesky of S + eps I fails, with the FP64 solver as well)
-MODES = {"fp64": (0, "f64", 1e-12, 1e-6), "bf16x3": (1, "mixed-bf16x3", 1e-8, 1e-3),
-         "tf32x3": (2, "mixed-tf32x3", 1e-8, 1e-3)}
+# mode -> (precision enum, dtype label, SVD cutoff, regulariser eps).  Every mode solves with
+# eps = 1e-6: the mixed modes' overlap is an exact Gram of fixed-point CWFs (positive
+# semidefinite to rounding), so they need no larger shift than FP64.
+MODES = {"fp64": (0, "f64", 1e-12, 1e-6), "bf16x3": (1, "mixed-bf16x3", 1e-8, 1e-6),
+         "tf32x3": (2, "mixed-tf32x3", 1e-8, 1e-6)}
 NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 (vector and DMMA alike), nominal
 # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz = 40.3e12 lane operations/s.  The mixed modes factorise
 # in double-float arithmetic on it: one complex multiply-add (8 flops) costs 39 FP32 operations
@@ -77,16 +77,34 @@ def parse():
     ap.add_argument("--workload", default="shin_metiu", choices=["shin_metiu", "cavity"],
                     help="Shin-Metiu 1024 x 512 (default) or the cavity 2048 x 256")
     ap.add_argument("--lam", type=float, default=0.5, help="cavity coupling lambda")
+    ap.add_argument("--eps", type=float, default=None, help="override the mode's regulariser")
+    ap.add_argument("--overlap-split", action="store_true",
+                    help="mixed modes: S from the split products (FP32 accumulation) instead of "
+                         "the exact fixed-point Gram")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the rank-error, mixed-vs-FP64 and cavity reports")
     return ap.parse_args()
 
 
+_WORKLOADS = {}
+
+
+CAVITY_EPS = 1e-4   # the cavity's regulariser in every mode (its coefficient equation is stiff)
+
+
 def make_workload(n_traj, cutoff, eps, nx=1024, nR=512, kind="shin_metiu", lam=0.5):
+    """The synthetic workload (tables built once per grid and model, then re-parameterised).
+    The cavity keeps its own dt (0.01) and eps (CAVITY_EPS)."""
     from workloads import WORKLOADS
+    key = (kind, nx, nR, lam)
+    if key not in _WORKLOADS:
+        if kind == "cavity":
+            _WORKLOADS[key] = WORKLOADS["cavity"](lam=lam)
+        else:
+            _WORKLOADS[key] = WORKLOADS["sm_paper"](nx=nx, nR=nR)
     if kind == "cavity":
-        return WORKLOADS["cavity"](n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps, lam=lam)
-    return WORKLOADS["sm_paper"](n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps, nx=nx, nR=nR)
+        eps = max(eps, CAVITY_EPS)
+    return _WORKLOADS[key].with_(n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps)
 
 
 def workload_name(w):
@@ -312,9 +330,12 @@ def run_ours(args, rank, ws, local):
 
     torch.cuda.set_device(local)
     prec, dtype_name, cutoff, eps = MODES[args.mode]
+    if args.eps is not None:
+        eps = args.eps
     w = make_workload(args.n_traj, cutoff, eps, args.nx, args.nR, args.workload, args.lam)
     params = g.params_from(w, precision=prec, solve_fp64=int(args.solve == "fp64"),
-                           coeff_scheme=int(args.coeff_scheme == "frozen"))
+                           coeff_scheme=int(args.coeff_scheme == "frozen"),
+                           overlap_split=int(args.overlap_split))
 
     sim = g.Icwf(params, w.V)
     sim.set_projectors(w.phi)
@@ -347,6 +368,9 @@ def run_ours(args, rank, ws, local):
         "config": {"workload": workload_name(w), "nx": w.nx, "nR": w.nR, "n_traj": w.n_traj,
                    "dt": w.dt, "rank_k": info["rank"], "svd_rel_cutoff": cutoff, "s_reg_eps": eps,
                    "svd_tail_rel": info["tail_rel"], "coeff_scheme": "rk4-" + args.coeff_scheme,
+                   "overlap": ("fp64" if args.mode == "fp64" else
+                               "split products, FP32 accumulation" if args.overlap_split else
+                               "exact Gram of 4-digit fixed-point CWFs (BF16 tensor cores)"),
                    "solve": ("fp64" if args.mode == "fp64" or args.solve == "fp64"
                              else "double-float (FP32 pairs)"),
                    "obs_every": OBS_EVERY, "obs_calls_timed": n_obs,
@@ -370,7 +394,8 @@ def run_ours(args, rank, ws, local):
     if rank == 0 and not args.no_exact2d:
         out["exact2d"] = run_exact2d(w)
     if rank == 0 and args.vs_exact > 0:
-        out["vs_exact"] = run_vs_exact(w, prec, args.vs_exact, args.vs_exact_every, w.seed)
+        out["vs_exact"] = run_vs_exact(w, prec, args.vs_exact, args.vs_exact_every, w.seed,
+                                       int(args.overlap_split))
     if rank == 0 and args.serving_jobs > 0:
         out["serving"] = run_serving(args.serving_jobs)
     if rank == 0 and not args.no_cpu:
@@ -453,14 +478,14 @@ def run_exact2d(w, steps=50, warmup=2):
                          "frac": flops * steps / dt / 1e12 / NOMINAL_FP64_TFLOPS}}
 
 
-def run_vs_exact(w, prec, steps, every, seed):
+def run_vs_exact(w, prec, steps, every, seed, overlap_split=0):
     """ICWF against the exact propagation of the full Psi(x, R) from the same Psi0 on the same
     grid (the paper's comparison in Figs. 1-2): L1 errors of the reduced densities and the largest
     BO-population error at every `every` steps.  ICWF starts from the sampled trajectories, so
     the t = 0 row shows the error of the initial representation."""
     import numpy as np
     import paper_1805_11169_gb300 as g
-    sim = g.Icwf(g.params_from(w, precision=prec), w.V)
+    sim = g.Icwf(g.params_from(w, precision=prec, overlap_split=overlap_split), w.V)
     sim.set_projectors(w.phi)
     sim.init_from_density(w.psi0, seed)
     ex = g.Exact2D(g.params_from(w), w.V)
@@ -573,7 +598,8 @@ def run_mixed_vs_fp64(mode, eps_mixed, steps=100):
 
 def run_cavity_line(args, local, peaks, steps=50, warmup=3):
     """Throughput of the same mode on the cavity workload (2048 x 256, lambda 0.5, N = 1024,
-    dt = 0.05; V_c exactly rank 1), timed like the headline, with its own roofline entry."""
+    dt = 0.01, eps = 1e-4; V_c exactly rank 1), timed like the headline, with its own roofline
+    entry."""
     import paper_1805_11169_gb300 as g
     prec, _, cutoff, eps = MODES[args.mode]
     w = make_workload(1024, cutoff, eps, kind="cavity", lam=args.lam)
@@ -584,7 +610,8 @@ def run_cavity_line(args, local, peaks, steps=50, warmup=3):
     total_ms, prof, launches, clocks, n_obs = timed_steps(sim, steps, warmup, local)
     sim.close()
     prof_step = {f: v for f, v in prof.items() if v[1] > 0 and f != "observables"}
-    return {"workload": workload_name(w), "value": w.n_traj * steps / (total_ms / 1e3),
+    return {"workload": workload_name(w), "s_reg_eps": w.s_reg_eps,
+            "value": w.n_traj * steps / (total_ms / 1e3),
             "unit": "trajectory-steps/s", "ms_per_step": total_ms / steps, "steps": steps,
             "rank_k": k, "obs_calls_timed": n_obs, "gpu_launches": int(launches),
             "roofline": roofline(prof_step, w, k, args.mode, peaks, args.solve),
@@ -603,7 +630,7 @@ def _model_library(rng):
                               dt=0.05, n_traj=64, svd_rel_cutoff=1e-8, s_reg_eps=1e-4))
     for nx, nq in ((512, 128), (1024, 128)):
         lib.append(cavity(nx=nx, x_range=(-60.0, 60.0), nq=nq, q_range=(-20.0, 20.0),
-                          lam=float(rng.uniform(0.1, 1.0)), dt=0.05, n_traj=64,
+                          lam=float(rng.uniform(0.1, 1.0)), dt=0.01, n_traj=64,
                           svd_rel_cutoff=1e-8, s_reg_eps=1e-4))
     return lib
 
