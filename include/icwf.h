@@ -51,10 +51,13 @@ typedef enum {
 } icwf_status;
 
 typedef enum {
-  ICWF_FP64 = 0,          /* CWFs complex128; matrix elements, solve and RK4 in FP64 */
+  ICWF_FP64 = 0,          /* CWFs complex128; matrix elements, Cholesky, triangular solves and
+                             RK4 in FP64 */
   ICWF_MIXED_BF16X3 = 1,  /* CWFs complex64, FP32 propagation; Grams on tcgen05 tensor cores as
                              three BF16 products (hi*hi + hi*lo + lo*hi), FP32 accumulation;
-                             S and Heff stored in FP64; S + eps*I formed in FP64; Cholesky and
+                             the overlap S as an exact Gram of fixed-point CWFs (positive
+                             semidefinite; see overlap_split); S and Heff stored in FP64;
+                             S + eps*I formed in FP64; Cholesky and
                              triangular solves in double-float arithmetic (pairs of FP32, about
                              44-48 significant bits) unless solve_fp64 is set; right-hand sides,
                              RK4 update and reductions in FP64 */

@@ -322,7 +322,9 @@ void solve(icwf_ctx* h, const double2* Lf, const double2* D, const double2* y, d
 
 void assemble(icwf_ctx* h, double2* S, double2* Hm) {
   ProfScope ps(h, F_ASSEMBLE);
-  h->launches += h->mixed ? 3 : 1;   // operand planes (two sides) + Grams, or the FP64 kernel
+  // operand planes (two sides) + Grams [+ digit planes (two sides) + exact overlap], or the FP64
+  // kernel
+  h->launches += h->mixed ? (h->p.overlap_split ? 3 : 6) : 1;
   JobView j = view(h);
   if (h->mixed) {
     launch_assemble_tc(j, h->p.precision, h->p.overlap_split == 0, S, Hm, h->tc_scratch,

@@ -1,11 +1,12 @@
 // FP64 linear algebra of the coefficient update (Eq. coeff, S dC/dt = -i Heff C): the
 // Tikhonov-shifted overlap S + eps I, its blocked Cholesky factorisation, the two triangular
 // solves, the Heff matrix-vector products of the RK4 stages and the final RK4 combination.
-// All arithmetic is FP64 in every precision mode (S is near-singular as CWFs overlap).
+// All arithmetic here is FP64 (S is near-singular as CWFs overlap).  The FP64 mode and the
+// solve_fp64 option of the mixed modes factorise and solve with these kernels; the mixed modes'
+// default solver is the double-float one of k_linalg_df.cu.
 #include <cuda_runtime.h>
 
 #include "icwf_internal.h"
-#include "df64.cuh"
 #include "k_common.cuh"
 
 namespace icwf {
@@ -48,150 +49,139 @@ struct MatBatch { double2* m[2]; double* inv[2]; double2* D[2]; };
 
 constexpr int PF_THREADS = 256;
 
-DF_HD cdf cdf_from(double2 z) { return cdf_make(df_from(z.x), df_from(z.y)); }
-DF_HD double2 cdf_to(cdf z) { return make_double2(df_to(z.re), df_to(z.im)); }
 
-// Factor the diagonal block jb of each matrix (one CTA per matrix).  The 32 x 32 block is
-// converted to double-float (FP32 pairs, ~48 bits) in shared memory, so the column-by-column
-// pivot chain (pivot -> 1/sqrt -> next pivot) runs on FP32 instructions, whose latency is a small
-// fraction of FP64's on this GPU.  Column c: y = 1/sqrt(A_cc) (Newton from an FP32 seed),
-// L_cc = A_cc y; the trailing triangle takes the rank-1 update A_rq -= A_rc conj(A_qc) y^2 from
-// the unscaled column, which is scaled (L_rc = A_rc y) one column later, when nothing reads it
-// any more: two barriers per column.  Outputs (FP64): L in place and the reciprocal pivots.
-// Rows and columns beyond N are treated as identity so that ragged sizes factor cleanly.
+// Factor the diagonal block jb of each matrix (one CTA per matrix) in FP64.  Column c:
+// y = 1/sqrt(A_cc), L_cc = A_cc y; the trailing triangle takes the rank-1 update
+// A_rq -= A_rc conj(A_qc) y^2 from the unscaled column, which is scaled (L_rc = A_rc y) one column
+// later, when nothing reads it any more.  Thread 0 updates the next pivot first (pair (c+1, c+1))
+// and computes its reciprocal square root while the other threads finish the rank-1 update, so
+// each column needs a single barrier.  Outputs: L in place and the reciprocal pivots.  Rows and
+// columns beyond N are treated as identity so that ragged sizes factor cleanly.
+__device__ __forceinline__ double rsqrt_ieee(double d) { return 1.0 / sqrt(d); }
+__device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) { return cmul(a, cconj(b)); }
+
 __global__ void __launch_bounds__(PF_THREADS) k_potrf_diag(int N, MatBatch mb, int jb, int* status) {
-  __shared__ cdf L[NB][NB + 1];
-  __shared__ df yv[NB];
-  __shared__ df y2b[2];   // y^2 of the current column, double-buffered by column parity
+  __shared__ double2 L[NB][NB + 1];
+  __shared__ double yv[NB];
+  __shared__ double y2b[2];   // y^2 of the current column, double-buffered by column parity
   double2* A = mb.m[blockIdx.y];
   double* inv = mb.inv[blockIdx.y];
   const int r0 = jb * NB;
-  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
   for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
     const int r = e / NB, c = e % NB;
     double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
     if (c <= r && r0 + r < N && r0 + c < N) v = A[(size_t)(r0 + r) * N + r0 + c];
-    L[r][c] = cdf_from(v);
+    L[r][c] = v;
   }
   __syncthreads();
-  // pivot 0; afterwards thread 0 updates the next pivot first (pair e = 0 is (c+1, c+1)) and
-  // computes its reciprocal square root while the other threads finish the rank-1 update, so
-  // each column needs a single barrier
   if (threadIdx.x == 0) {
-    df d = L[0][0].re;
-    if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
-    const df y = df_rsqrt(d);
-    L[0][0] = cdf_make(df_mul(d, y), zero);
+    double d = L[0][0].x;
+    if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
+    const double y = rsqrt_ieee(d);
+    L[0][0] = make_double2(d * y, 0.0);
     yv[0] = y;
-    y2b[0] = df_mul(y, y);
+    y2b[0] = y * y;
   }
   __syncthreads();
   for (int c = 0; c < NB; ++c) {
     if (c > 0) {
       // column c-1 is no longer read: scale it now
       const int r = c + (int)threadIdx.x;
-      if (r < NB) L[r][c - 1] = cdf_scale(L[r][c - 1], yv[c - 1]);
+      if (r < NB) L[r][c - 1] = cscale(L[r][c - 1], yv[c - 1]);
     }
-    const df y2 = y2b[c & 1];
+    const double y2 = y2b[c & 1];
     // lower-triangle pairs c < q <= r: thread t takes row c + 1 + t/8 and every 8th column
     const int r = c + 1 + (int)(threadIdx.x >> 3);
     for (int q = c + 1 + (int)(threadIdx.x & 7); r < NB && q <= r; q += 8) {
-      L[r][q] = cdf_sub(L[r][q], cdf_scale(cdf_mul_conj(L[r][c], L[q][c]), y2));
+      L[r][q] = csub(L[r][q], cscale(cmul_conj(L[r][c], L[q][c]), y2));
       if (threadIdx.x == 0) {
         // thread 0 just produced the pivot of column c + 1
-        df d = L[c + 1][c + 1].re;
-        if (!(d.h > 0.f)) { set_flag(status, ST_CHOL); d = one; }
-        const df y = df_rsqrt(d);
-        L[c + 1][c + 1] = cdf_make(df_mul(d, y), zero);
+        double d = L[c + 1][c + 1].x;
+        if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
+        const double y = rsqrt_ieee(d);
+        L[c + 1][c + 1] = make_double2(d * y, 0.0);
         yv[c + 1] = y;
-        y2b[(c + 1) & 1] = df_mul(y, y);
+        y2b[(c + 1) & 1] = y * y;
       }
     }
     __syncthreads();
   }
-  // column NB-1 has no entries below the diagonal; store
   for (int e = threadIdx.x; e < NB * NB; e += PF_THREADS) {
     const int r = e / NB, c = e % NB;
-    if (c <= r && r0 + r < N && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = cdf_to(L[r][c]);
+    if (c <= r && r0 + r < N && r0 + c < N) A[(size_t)(r0 + r) * N + r0 + c] = L[r][c];
   }
-  if (threadIdx.x < NB && r0 + threadIdx.x < N) inv[r0 + threadIdx.x] = df_to(yv[threadIdx.x]);
+  if (threadIdx.x < NB && r0 + threadIdx.x < N) inv[r0 + threadIdx.x] = yv[threadIdx.x];
 }
 
 constexpr int TR_WARPS = 8;   // rows per panel-solve CTA
 
-// Panel solve A_ib <- A_ib L_bb^-H below the diagonal block jb: one warp per row, lane = column,
-// column-oriented substitution x_m = a_m / L_mm, a_c -= x_m conj(L_cm) (c > m) in double-float,
-// so that the 32-step chain runs on FP32 latencies.  Inputs and outputs are FP64.
+// Panel solve A_ib <- A_ib L_bb^-H below the diagonal block jb in FP64: one warp per row, lane =
+// column, column-oriented substitution x_m = a_m / L_mm, a_c -= x_m conj(L_cm) (c > m).
 __global__ void __launch_bounds__(TR_WARPS * 32) k_trsm_panel(int N, MatBatch mb, int jb) {
-  __shared__ cdf Ls[NB][NB + 1];
-  __shared__ df ys[NB];
+  __shared__ double2 Ls[NB][NB + 1];
+  __shared__ double ys[NB];
   double2* A = mb.m[blockIdx.y];
   const double* inv = mb.inv[blockIdx.y];
   const int c0 = jb * NB;
-  const df zero = df_make(0.f, 0.f);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
     double2 l = make_double2(0.0, 0.0);
     if (c < r && c0 + r < N && c0 + c < N) l = A[(size_t)(c0 + r) * N + c0 + c];
-    Ls[r][c] = cdf_from(l);
+    Ls[r][c] = l;
   }
-  if (threadIdx.x < NB) ys[threadIdx.x] = df_from((c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : 1.0);
+  if (threadIdx.x < NB) ys[threadIdx.x] = (c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : 1.0;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = (jb + 1) * NB + blockIdx.x * TR_WARPS + warp;
   if (row >= N) return;
   const bool cok = c0 + lane < N;
-  cdf a = cdf_from(cok ? A[(size_t)row * N + c0 + lane] : make_double2(0.0, 0.0));
+  double2 a = cok ? A[(size_t)row * N + c0 + lane] : make_double2(0.0, 0.0);
 #pragma unroll 4
   for (int m = 0; m < NB; ++m) {
-    const cdf xs = cdf_scale(a, ys[m]);
-    cdf x;
-    x.re.h = __shfl_sync(0xffffffffu, xs.re.h, m);
-    x.re.l = __shfl_sync(0xffffffffu, xs.re.l, m);
-    x.im.h = __shfl_sync(0xffffffffu, xs.im.h, m);
-    x.im.l = __shfl_sync(0xffffffffu, xs.im.l, m);
+    const double2 xs = cscale(a, ys[m]);
+    double2 x;
+    x.x = __shfl_sync(0xffffffffu, xs.x, m);
+    x.y = __shfl_sync(0xffffffffu, xs.y, m);
     if (lane == m) a = x;
-    else if (lane > m) a = cdf_sub(a, cdf_mul_conj(x, Ls[lane][m]));
+    else if (lane > m) a = csub(a, cmul_conj(x, Ls[lane][m]));
   }
-  (void)zero;
-  if (cok) A[(size_t)row * N + c0 + lane] = cdf_to(a);
+  if (cok) A[(size_t)row * N + c0 + lane] = a;
 }
 
 // Inverse of every diagonal block after the factorisation: D_b = L_bb^-1 (lower triangular),
-// row-major per block in D[(b*32 + r)*32 + c], one CTA per block, all blocks at once.
-// Right-looking elimination in double-float: for k = 0..31, row k of D is scaled by 1/L_kk (it is
-// then final) and removed from the rows below with the multipliers L_rk.
+// row-major per block in D[(b*32 + r)*32 + c], one CTA per block, all blocks at once, in FP64.
+// Right-looking elimination: for k = 0..31, row k of D is scaled by 1/L_kk (it is then final) and
+// removed from the rows below with the multipliers L_rk.
 __global__ void __launch_bounds__(128) k_trtri_diag(int N, MatBatch mb) {
-  __shared__ cdf Ls[NB][NB + 1];
-  __shared__ cdf Dm[NB][NB + 1];
-  __shared__ df ys[NB];
+  __shared__ double2 Ls[NB][NB + 1];
+  __shared__ double2 Dm[NB][NB + 1];
+  __shared__ double ys[NB];
   const double2* A = mb.m[blockIdx.y];
   const double* inv = mb.inv[blockIdx.y];
   double2* D = mb.D[blockIdx.y];
   const int jb = blockIdx.x, r0 = jb * NB;
-  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
     double2 l = make_double2(0.0, 0.0);
     if (c < r && r0 + r < N && r0 + c < N) l = A[(size_t)(r0 + r) * N + r0 + c];
-    Ls[r][c] = cdf_from(l);
-    Dm[r][c] = cdf_make(r == c ? one : zero, zero);
+    Ls[r][c] = l;
+    Dm[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
   }
-  if (threadIdx.x < NB) ys[threadIdx.x] = df_from((r0 + threadIdx.x < N) ? inv[r0 + threadIdx.x] : 1.0);
+  if (threadIdx.x < NB) ys[threadIdx.x] = (r0 + threadIdx.x < N) ? inv[r0 + threadIdx.x] : 1.0;
   __syncthreads();
   for (int k = 0; k < NB; ++k) {
-    if (threadIdx.x <= k) Dm[k][threadIdx.x] = cdf_scale(Dm[k][threadIdx.x], ys[k]);
+    if (threadIdx.x <= k) Dm[k][threadIdx.x] = cscale(Dm[k][threadIdx.x], ys[k]);
     __syncthreads();
     const int rows = NB - 1 - k, cols = k + 1;
     for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
       const int r = k + 1 + e / cols, c = e % cols;
-      Dm[r][c] = cdf_sub(Dm[r][c], cdf_mul(Ls[r][k], Dm[k][c]));
+      Dm[r][c] = csub(Dm[r][c], cmul(Ls[r][k], Dm[k][c]));
     }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
-    if (r0 + r < N) D[((size_t)jb * NB + r) * NB + c] = cdf_to(Dm[r][c]);
+    if (r0 + r < N) D[((size_t)jb * NB + r) * NB + c] = Dm[r][c];
   }
 }
 
