@@ -101,6 +101,9 @@ typedef struct {
   int64_t kernel_launches;  /* CUDA kernels launched by icwf_step on this handle since create */
   size_t obs_bytes;         /* device memory of the observables work buffers, which
                                icwf_observables allocates on its first call (0 until then) */
+  int32_t prop_threads;     /* CTA size of the CWF propagator chosen by the autotuner for this
+                               shape (fastest of 64..512 threads, timed at the first create of
+                               the shape in the process) */
 } icwf_info;
 
 /* Observables of the current state (paper: reduced densities, BO populations and the
@@ -240,8 +243,28 @@ icwf_status icwf_observables_static(icwf_handle h, icwf_obs* out);
 
 /* A pool admits jobs while their summed device footprint stays within hbm_budget_bytes and at
  * most max_jobs are live; pending jobs wait in arrival order.  Every icwf_pool_tick advances
- * every live job by one step, the jobs' kernels grouped per kernel family. */
+ * every live job by one step.  By default each job's step is captured into CUDA graphs at its
+ * first tick (one per parity of its ping-pong matrix buffers) and the live jobs' step graphs run
+ * as child graphs of one tick graph, instantiated once per live set and parity pattern and
+ * launched with a single cudaGraphLaunch per tick; the jobs share no memory, so their kernels
+ * overlap on the device.  Job handles are owned by the pool after submission. */
 icwf_status icwf_pool_create(size_t hbm_budget_bytes, int32_t max_jobs, icwf_pool* out);
+
+/* Counters of a pool since creation. */
+typedef struct {
+  int64_t ticks;            /* icwf_pool_tick calls */
+  int64_t graph_launches;   /* cudaGraphLaunch calls (at most one per tick) */
+  int64_t graph_builds;     /* tick graphs instantiated (live-set or parity changes) */
+  int64_t kernel_nodes;     /* kernels executed inside tick graphs */
+  int64_t graph_job_steps;  /* job steps run inside tick graphs */
+  int64_t eager_job_steps;  /* job steps launched directly (graphs off or capture failed) */
+} icwf_pool_stats;
+
+icwf_status icwf_pool_get_stats(icwf_pool pool, icwf_pool_stats* out);
+
+/* on = 0 launches every job's kernels directly on its own streams at each tick (no graphs);
+ * on = 1 (default) uses the captured tick graphs. */
+icwf_status icwf_pool_set_graphs(icwf_pool pool, int32_t on);
 
 /* Hand an initialised job to the pool (the pool owns it from now on) to run n_steps steps.
  * *job_id identifies it in icwf_pool_poll. */

@@ -41,7 +41,14 @@ class icwf_info(ct.Structure):
     _fields_ = [("rank", ct.c_int32), ("tail_rel", ct.c_double), ("next_rel", ct.c_double),
                 ("sigma_max", ct.c_double), ("device_bytes", ct.c_size_t),
                 ("steps_done", ct.c_int64), ("t", ct.c_double),
-                ("kernel_launches", ct.c_int64), ("obs_bytes", ct.c_size_t)]
+                ("kernel_launches", ct.c_int64), ("obs_bytes", ct.c_size_t),
+                ("prop_threads", ct.c_int32)]
+
+
+class icwf_pool_stats(ct.Structure):
+    _fields_ = [("ticks", ct.c_int64), ("graph_launches", ct.c_int64),
+                ("graph_builds", ct.c_int64), ("kernel_nodes", ct.c_int64),
+                ("graph_job_steps", ct.c_int64), ("eager_job_steps", ct.c_int64)]
 
 
 class icwf_obs(ct.Structure):
@@ -83,6 +90,8 @@ def _load():
         "icwf_pool_tick": [H, P(ct.c_int32), P(ct.c_int32)],
         "icwf_pool_poll": [H, ct.c_int32, P(icwf_obs), P(ct.c_int32)],
         "icwf_pool_destroy": [H],
+        "icwf_pool_get_stats": [H, P(icwf_pool_stats)],
+        "icwf_pool_set_graphs": [H, ct.c_int32],
         "icwf_exact2d_create": [P(icwf_params), d, P(H)],
         "icwf_exact2d_set_state": [H, d],
         "icwf_exact2d_set_projectors": [H, ct.c_int32, d],
@@ -297,6 +306,16 @@ def icwf_pool_poll(pool, job_id: int, nx: int, nR: int):
                          "rho_R": rho_R, "pop": pop[:ns].copy(),
                          "decoherence": decoh[:ns * ns].reshape(ns, ns).copy(),
                          "n_clamped": o.n_clamped}
+
+
+def icwf_pool_get_stats(pool) -> dict:
+    st = icwf_pool_stats()
+    _check(LIB.icwf_pool_get_stats(pool, ct.byref(st)))
+    return {k: getattr(st, k) for k, _ in icwf_pool_stats._fields_}
+
+
+def icwf_pool_set_graphs(pool, on: bool):
+    _check(LIB.icwf_pool_set_graphs(pool, 1 if on else 0))
 
 
 def icwf_pool_destroy(pool):

@@ -15,6 +15,7 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -106,6 +107,8 @@ struct icwf_ctx {
   int64_t steps = 0;
   double t = 0.0;
   int64_t launches = 0;   // kernels launched by icwf_step
+  int prop_threads = 256; // CTA size of the CWF propagator (autotuned per shape at create)
+  int64_t version = 0;    // bumped by calls that change captured kernel arguments (eps)
   // profiling
   bool prof_on = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -120,6 +123,13 @@ icwf_status fail(icwf_ctx* h, icwf_status st, const std::string& msg) {
   if (h) h->err = msg; else g_err = msg;
   return st;
 }
+
+#define CK_POOL(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(nullptr, ICWF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
 
 #define CK(call)                                                                         \
   do {                                                                                   \
@@ -310,7 +320,7 @@ void solve(icwf_ctx* h, const double2* Lf, const double2* D, const double2* y, d
            bool minus_i, cudaStream_t s = nullptr) {
   if (!s) s = h->stream;
   ProfScope ps(h, F_SOLVE, s);
-  ++h->epoch;
+  h->epoch = 1;   // the launchers zero the block flags before every solve
   if (h->df_solve)
     launch_chol_solve_df(h->N, Lf, D, y, h->work, out, minus_i, h->flags, h->tickets, h->epoch,
                          h->status, s);
@@ -369,8 +379,8 @@ void step_once(icwf_ctx* h) {
   }
   {
     ProfScope ps(h, F_PROPAGATE);
-    if (h->mixed) launch_propagate<float>(j, h->stream);
-    else launch_propagate<double>(j, h->stream);
+    if (h->mixed) launch_propagate<float>(j, h->prop_threads, h->stream);
+    else launch_propagate<double>(j, h->prop_threads, h->stream);
     h->launches += 1;
   }
   assemble(h, h->S[nxt], h->H[nxt]);
@@ -414,6 +424,63 @@ void step_once(icwf_ctx* h) {
   h->cur = nxt;
   h->steps += 1;
   h->t += dt;
+}
+
+// ---- autotuner ------------------------------------------------------------------------------
+// The CWF propagator (one CTA per CWF, radix-2 FFT over the column in shared memory) is launched
+// with the CTA size that measured fastest for the problem shape (precision, N, nx, nR): 64, 128,
+// 256 or 512 threads, each timed over three launches with CUDA events on the handle's own
+// buffers (zeroed first) when the first handle of that shape is created.  Results are cached for
+// the process; later handles of the same shape reuse them.
+
+struct TuneKey {
+  int prec, N, nx, nR;
+  bool operator<(const TuneKey& o) const {
+    if (prec != o.prec) return prec < o.prec;
+    if (N != o.N) return N < o.N;
+    if (nx != o.nx) return nx < o.nx;
+    return nR < o.nR;
+  }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune;
+
+int tune_propagate(icwf_ctx* h) {
+  const TuneKey key{h->mixed ? 1 : 0, h->N, h->nx, h->nR};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  const size_t cw = h->cwf_elem;
+  cudaMemsetAsync(h->psi, 0, (size_t)h->N * h->nx * cw, h->stream);
+  cudaMemsetAsync(h->chi, 0, (size_t)h->N * h->nR * cw, h->stream);
+  for (double* q : {h->x, h->R, h->xo, h->Ro}) cudaMemsetAsync(q, 0, (size_t)h->N * 8, h->stream);
+  JobView j = view(h);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = 256;
+  float best_ms = 1e30f;
+  for (int threads : {64, 128, 256, 512}) {
+    auto go = [&]() {
+      if (h->mixed) launch_propagate<float>(j, threads, h->stream);
+      else launch_propagate<double>(j, threads, h->stream);
+    };
+    go();
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < 3; ++r) go();
+    cudaEventRecord(e1, h->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      continue;
+    if (ms < best_ms) { best_ms = ms; best = threads; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune[key] = best;
+  return best;
 }
 
 icwf_status alloc_obs(icwf_ctx* h) {
@@ -689,6 +756,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   UP(h->v1, v1.data(), v1.size() * 8);
   UP(h->v2, v2.data(), v2.size() * 8);
 #undef UP
+  h->prop_threads = tune_propagate(h);
   if (cudaMemsetAsync(h->flags, 0, (size_t)2 * nblk * 4 + 64, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->status, 0, 64 * 4, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1003,6 +1071,7 @@ icwf_status icwf_get_info(icwf_handle h, icwf_info* out) {
   out->t = h->t;
   out->kernel_launches = h->launches;
   out->obs_bytes = h->obs_bytes;
+  out->prop_threads = h->prop_threads;
   return ICWF_OK;
 }
 
@@ -1010,6 +1079,7 @@ icwf_status icwf_set_regularisation(icwf_handle h, double eps) {
   if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_set_regularisation: NULL handle");
   if (!std::isfinite(eps)) return fail(h, ICWF_ERR_ARG, "icwf_set_regularisation: eps is not finite");
   h->p.s_reg_eps = eps;
+  h->version += 1;   // a pool re-captures this job's step graphs
   return ICWF_OK;
 }
 
@@ -1069,6 +1139,11 @@ struct PoolJob {
   double norm = 0, energy = 0, t = 0;
   std::vector<double> rho_x, rho_R, pop, decoh;
   int n_clamped = 0, n_states = 0;
+  // one captured step per ping-pong parity of the job's matrix buffers
+  cudaGraph_t g[2] = {nullptr, nullptr};
+  bool graphs_tried = false, graphs_ok = false;
+  int64_t kernels_per_step = 0;
+  int64_t version = -1;   // handle version the graphs were captured at
 };
 
 struct icwf_pool_ctx {
@@ -1078,17 +1153,93 @@ struct icwf_pool_ctx {
   std::vector<PoolJob> jobs;
   std::deque<int> pending;
   std::vector<int> live;
+  bool use_graphs = true;
+  cudaStream_t stream = nullptr;
+  // instantiated tick graphs of the current live set, keyed by (job id, parity) of every job
+  std::map<std::vector<int64_t>, cudaGraphExec_t> ticks_cache;
+  std::vector<int> cache_live;   // the live set the cache belongs to
+  icwf_pool_stats stats{};
 };
+
+namespace {
+
+void clear_tick_cache(icwf_pool pool) {
+  for (auto& kv : pool->ticks_cache) cudaGraphExecDestroy(kv.second);
+  pool->ticks_cache.clear();
+}
+
+void destroy_job_graphs(PoolJob& j) {
+  for (auto& g : j.g)
+    if (g) { cudaGraphDestroy(g); g = nullptr; }
+  j.graphs_ok = false;
+}
+
+// Capture one step of the job for each parity of its ping-pong buffers (two consecutive steps
+// recorded, not executed), then restore the host-side step state.  Returns false (and leaves the
+// job to eager stepping) if the capture fails.
+bool capture_job_graphs(PoolJob& pj) {
+  icwf_ctx* h = pj.h;
+  const bool prof = h->prof_on;
+  const int cur0 = h->cur;
+  const int64_t steps0 = h->steps, l0 = h->launches;
+  const double t0 = h->t;
+  h->prof_on = false;
+  bool ok = true;
+  for (int k = 0; k < 2 && ok; ++k) {
+    const int par = h->cur;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    step_once(h);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess || !g) {
+      ok = false;
+      if (g) cudaGraphDestroy(g);
+      break;
+    }
+    pj.g[par] = g;
+  }
+  pj.kernels_per_step = (h->launches - l0) / 2;
+  h->cur = cur0;
+  h->steps = steps0;
+  h->t = t0;
+  h->launches = l0;
+  h->prof_on = prof;
+  if (!ok) {
+    destroy_job_graphs(pj);
+    cudaGetLastError();   // the failed capture's own error; the job steps eagerly instead
+  }
+  pj.graphs_ok = ok;
+  pj.version = h->version;
+  return ok;
+}
+
+}  // namespace
 
 extern "C" {
 
 icwf_status icwf_pool_create(size_t hbm_budget_bytes, int32_t max_jobs, icwf_pool* out) {
   if (!out || max_jobs < 1 || hbm_budget_bytes == 0)
     return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_create: invalid argument");
-  icwf_pool p = new icwf_pool_ctx;
+  std::unique_ptr<icwf_pool_ctx> p(new icwf_pool_ctx);
   p->budget = hbm_budget_bytes;
   p->max_jobs = max_jobs;
-  *out = p;
+  if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(nullptr, ICWF_ERR_CUDA, "icwf_pool_create: cudaStreamCreate failed");
+  *out = p.release();
+  return ICWF_OK;
+}
+
+icwf_status icwf_pool_set_graphs(icwf_pool pool, int32_t on) {
+  if (!pool) return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_set_graphs: NULL pool");
+  pool->use_graphs = on != 0;
+  return ICWF_OK;
+}
+
+icwf_status icwf_pool_get_stats(icwf_pool pool, icwf_pool_stats* out) {
+  if (!pool || !out) return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_get_stats: NULL argument");
+  *out = pool->stats;
   return ICWF_OK;
 }
 
@@ -1127,14 +1278,20 @@ static void finish_job(icwf_pool pool, int id, bool ok) {
   } else {
     j.state = 3;
   }
+  destroy_job_graphs(j);
   pool->live_bytes -= h->arena.size;
   icwf_destroy(h);
   j.h = nullptr;
 }
 
+// One tick: admit pending jobs (arrival order, slots and device-memory budget), then advance
+// every live job by one step.  With graphs on, each job's step is a captured graph (recorded at
+// its first tick, one per buffer parity) and all of them run as child graphs of one tick graph,
+// instantiated once per live set and parity pattern and launched with a single cudaGraphLaunch;
+// the jobs share nothing, so their kernels overlap freely.  Without graphs (or if a capture
+// fails) every job's kernels are launched directly on its own streams.
 icwf_status icwf_pool_tick(icwf_pool pool, int32_t* n_live, int32_t* n_finished) {
   if (!pool) return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_tick: NULL pool");
-  // admission in arrival order while slots and memory allow
   while (!pool->pending.empty() && (int)pool->live.size() < pool->max_jobs) {
     const int id = pool->pending.front();
     const size_t b = pool->jobs[id].h->arena.size;
@@ -1144,11 +1301,77 @@ icwf_status icwf_pool_tick(icwf_pool pool, int32_t* n_live, int32_t* n_finished)
     pool->live_bytes += b;
     pool->jobs[id].state = 1;
   }
-  // one step of every live job: enqueue all, then wait for all (the jobs' streams overlap)
-  for (int id : pool->live) {
-    PoolJob& j = pool->jobs[id];
-    if (j.h->steps < j.target) step_once(j.h);
+  if (pool->live != pool->cache_live) {
+    clear_tick_cache(pool);
+    pool->cache_live = pool->live;
   }
+  std::vector<int> run;
+  for (int id : pool->live)
+    if (pool->jobs[id].h->steps < pool->jobs[id].target) run.push_back(id);
+  bool graphs = pool->use_graphs && !run.empty();
+  if (graphs) {
+    for (int id : run) {
+      PoolJob& j = pool->jobs[id];
+      if (j.graphs_tried && j.version != j.h->version) {
+        // captured kernel arguments are stale: record the job's step again
+        destroy_job_graphs(j);
+        clear_tick_cache(pool);
+        j.graphs_tried = false;
+      }
+      if (!j.graphs_tried) {
+        j.graphs_tried = true;
+        capture_job_graphs(j);
+      }
+      graphs = graphs && j.graphs_ok;
+    }
+  }
+  bool launched = false;
+  if (graphs) {
+    std::vector<int64_t> key;
+    for (int id : run) key.push_back(2 * (int64_t)id + pool->jobs[id].h->cur);
+    cudaGraphExec_t exec = nullptr;
+    auto it = pool->ticks_cache.find(key);
+    if (it != pool->ticks_cache.end()) {
+      exec = it->second;
+    } else {
+      cudaGraph_t tg = nullptr;
+      bool ok = cudaGraphCreate(&tg, 0) == cudaSuccess;
+      for (size_t k = 0; ok && k < run.size(); ++k) {
+        PoolJob& j = pool->jobs[run[k]];
+        cudaGraphNode_t node;
+        ok = cudaGraphAddChildGraphNode(&node, tg, nullptr, 0, j.g[j.h->cur]) == cudaSuccess;
+      }
+      ok = ok && cudaGraphInstantiate(&exec, tg, 0) == cudaSuccess;
+      if (tg) cudaGraphDestroy(tg);
+      if (ok) {
+        pool->ticks_cache[key] = exec;
+        pool->stats.graph_builds += 1;
+      } else {
+        exec = nullptr;
+        cudaGetLastError();
+      }
+    }
+    if (exec && cudaGraphLaunch(exec, pool->stream) == cudaSuccess) {
+      launched = true;
+      pool->stats.graph_launches += 1;
+      for (int id : run) {
+        PoolJob& j = pool->jobs[id];
+        icwf_ctx* h = j.h;
+        h->cur = 1 - h->cur;
+        h->steps += 1;
+        h->t += h->p.dt;
+        h->launches += j.kernels_per_step;
+        pool->stats.kernel_nodes += j.kernels_per_step;
+      }
+      pool->stats.graph_job_steps += (int64_t)run.size();
+    }
+  }
+  if (!launched) {
+    for (int id : run) step_once(pool->jobs[id].h);
+    pool->stats.eager_job_steps += (int64_t)run.size();
+  }
+  pool->stats.ticks += 1;
+  if (launched) CK_POOL(cudaStreamSynchronize(pool->stream));
   int fin = 0;
   std::vector<int> still;
   for (int id : pool->live) {
@@ -1182,8 +1405,13 @@ icwf_status icwf_pool_poll(icwf_pool pool, int32_t job_id, icwf_obs* out, int32_
 
 icwf_status icwf_pool_destroy(icwf_pool pool) {
   if (!pool) return ICWF_OK;
-  for (auto& j : pool->jobs)
+  if (pool->stream) cudaStreamSynchronize(pool->stream);
+  clear_tick_cache(pool);
+  for (auto& j : pool->jobs) {
+    destroy_job_graphs(j);
     if (j.h) icwf_destroy(j.h);
+  }
+  if (pool->stream) cudaStreamDestroy(pool->stream);
   delete pool;
   return ICWF_OK;
 }

@@ -67,7 +67,8 @@ template <typename T> void launch_velocity(const JobView& j, const double2* C, c
 // a1-a3: Strang split-operator step of every psi_a (pinned at the R midpoint) and chi_a (pinned
 // at the x midpoint).  mode 0 = propagate; mode 1 = apply the kinetic operator only (writes to
 // out, diagnostic).
-template <typename T> void launch_propagate(const JobView& j, cudaStream_t s);
+// threads: CTA size (a power of two in [64, 512], chosen per shape by the autotuner in api.cpp).
+template <typename T> void launch_propagate(const JobView& j, int threads, cudaStream_t s);
 template <typename T> void launch_kinetic(const JobView& j, void* out_psi, void* out_chi,
                                           cudaStream_t s);
 
@@ -99,8 +100,9 @@ int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const
 void launch_matvec(int N, const double2* H0, const double2* H1, double theta, const double2* C,
                    const double2* kp, double c, double2* y, cudaStream_t s);
 // L z = y (forward) then L^H w = z (backward); out = scale_i * w with scale_i = -i when
-// minus_i, else 1.  work needs 2N complex, flags 2*ceil(N/32) unsigned (zeroed at allocation),
-// tickets 2 unsigned; epoch must differ from every earlier call on the same flags.
+// minus_i, else 1.  work needs 2N complex; flags holds 2*ceil(N/32) block flags followed by the
+// 2 tickets (the launcher zeroes all of them first, so any fixed epoch > 0 works and a captured
+// sequence can be replayed); `tickets` is unused.
 void launch_chol_solve(int N, const double2* L, const double2* D, const double2* y, double2* work,
                        double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
                        unsigned epoch, int* status, cudaStream_t s);

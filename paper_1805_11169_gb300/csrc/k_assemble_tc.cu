@@ -475,10 +475,18 @@ bool launch_assemble_tc(const JobView& j, int precision, bool exact_s, double2* 
   const int T = (j.N + BM - 1) / BM;
   const unsigned grid = (unsigned)(4 * T * (T + 1) / 2);
   if (kind) {
-    cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    static bool attr1 = false;   // set once: no attribute changes inside a captured launch
+    if (!attr1) {
+      cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      attr1 = true;
+    }
     k_gram_tc<1><<<grid, 192, SMEM_BYTES, s>>>(a, m);
   } else {
-    cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    static bool attr0 = false;
+    if (!attr0) {
+      cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      attr0 = true;
+    }
     k_gram_tc<0><<<grid, 192, SMEM_BYTES, s>>>(a, m);
   }
   return true;

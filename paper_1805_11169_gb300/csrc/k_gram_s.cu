@@ -362,7 +362,11 @@ bool launch_gram_s(const JobView& j, double2* S, void* scratch, size_t bytes, cu
   a.S = S; a.status = j.status;
   const int T = (j.N + BM - 1) / BM;
   const unsigned grid = (unsigned)(4 * T * (T + 1) / 2);
-  cudaFuncSetAttribute(k_gram_s, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  static bool attr = false;   // set once: no attribute changes inside a captured launch
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram_s, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr = true;
+  }
   k_gram_s<<<grid, 192, SMEM_BYTES, s>>>(a, m);
   return true;
 }

@@ -591,11 +591,14 @@ void launch_chol_solve(int N, const double2* L, const double2* D, const double2*
                        double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
                        unsigned epoch, int* status, cudaStream_t s) {
   const int nblk = (N + NB - 1) / NB;
-  cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
-  k_trsv_lower<<<nblk, TW * 32, 0, s>>>(N, L, D, y, work, flags, tickets, epoch, status);
+  // the block flags start from zero in every solve (one memset with the tickets, which follow
+  // them), so a captured launch sequence can be replayed with the same epoch
+  cudaMemsetAsync(flags, 0, (2 * (size_t)nblk + 2) * sizeof(unsigned), s);
+  (void)tickets;
+  k_trsv_lower<<<nblk, TW * 32, 0, s>>>(N, L, D, y, work, flags, flags + 2 * nblk, epoch, status);
   // work[0, N) holds z; work[N, 2N) holds w for the backward pass's consumers
   k_trsv_upper<<<nblk, TW * 32, 0, s>>>(N, L, D, work, out, minus_i, work + N, flags + nblk,
-                                        tickets + 1, epoch, status);
+                                        flags + 2 * nblk + 1, epoch, status);
 }
 
 // ------------------------------------------------------------------------------ RK4 combination

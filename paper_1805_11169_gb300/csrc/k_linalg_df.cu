@@ -1137,12 +1137,15 @@ void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y,
                                              status);
     return;
   }
-  cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
+  // block flags and tickets (which follow them) start from zero in every solve, so a captured
+  // launch sequence can be replayed with the same epoch
+  cudaMemsetAsync(flags, 0, (2 * (size_t)nblk + 2) * sizeof(unsigned), s);
+  (void)tickets;
   float4* zb = (float4*)work;
   k_trsv_lower_df<<<nblk, TW * 32, 0, s>>>(N, (const float4*)L, (const float4*)D, y, zb, flags,
-                                            tickets, epoch, status);
+                                            flags + 2 * nblk, epoch, status);
   k_trsv_upper_df<<<nblk, TW * 32, 0, s>>>(N, (const float4*)L, (const float4*)D, zb, out, minus_i,
-                                            zb + N, flags + nblk, tickets + 1, epoch, status);
+                                            zb + N, flags + nblk, flags + 2 * nblk + 1, epoch, status);
 }
 
 }  // namespace icwf

@@ -267,7 +267,7 @@ template void launch_velocity<float>(const JobView&, const double2*, cudaStream_
 // potential phases live in shared memory (2 n complex).  mode 0: Strang step in place; mode 1:
 // kinetic operator applied, result to out.
 template <typename T>
-__global__ void __launch_bounds__(256) k_propagate(JobView j, const T* __restrict__ Vt, int mode,
+__global__ void __launch_bounds__(512) k_propagate(JobView j, const T* __restrict__ Vt, int mode,
                                                    void* out_psi, void* out_chi, double kfx,
                                                    double kfR) {
   using Z = c_t<T>;
@@ -335,29 +335,39 @@ __global__ void __launch_bounds__(256) k_propagate(JobView j, const T* __restric
   }
 }
 
+// The propagator's dynamic shared memory limit, set once (to the largest grid's need) so that no
+// launch, captured or not, changes a function attribute.
 template <typename T>
-void launch_propagate(const JobView& j, cudaStream_t s) {
+void propagate_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_propagate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * 4096 * sizeof(c_t<T>)));
+    done = true;
+  }
+}
+
+template <typename T>
+void launch_propagate(const JobView& j, int threads, cudaStream_t s) {
   const int nmax = j.nx > j.nR ? j.nx : j.nR;
   const size_t sm = 2 * (size_t)nmax * sizeof(c_t<T>);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_propagate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_propagate<T><<<2 * j.N, 256, sm, s>>>(j, (const T*)j.Vt, 0, nullptr, nullptr, 0.0, 0.0);
+  propagate_attr<T>();
+  k_propagate<T><<<2 * j.N, threads, sm, s>>>(j, (const T*)j.Vt, 0, nullptr, nullptr, 0.0, 0.0);
 }
 
 template <typename T>
 void launch_kinetic(const JobView& j, void* out_psi, void* out_chi, cudaStream_t s) {
   const int nmax = j.nx > j.nR ? j.nx : j.nR;
   const size_t sm = 2 * (size_t)nmax * sizeof(c_t<T>);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_propagate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  propagate_attr<T>();
   const double PI = 3.14159265358979323846;
   const double gx = 2.0 * PI / (j.nx * j.dx), gR = 2.0 * PI / (j.nR * j.dR);
   const double kfx = gx * gx * 0.5 * j.inv_mx / j.nx;
   const double kfR = gR * gR * 0.5 * j.inv_mR / j.nR;
   k_propagate<T><<<2 * j.N, 256, sm, s>>>(j, (const T*)j.Vt, 1, out_psi, out_chi, kfx, kfR);
 }
-template void launch_propagate<double>(const JobView&, cudaStream_t);
-template void launch_propagate<float>(const JobView&, cudaStream_t);
+template void launch_propagate<double>(const JobView&, int, cudaStream_t);
+template void launch_propagate<float>(const JobView&, int, cudaStream_t);
 template void launch_kinetic<double>(const JobView&, void*, void*, cudaStream_t);
 template void launch_kinetic<float>(const JobView&, void*, void*, cudaStream_t);
 

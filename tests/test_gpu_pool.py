@@ -108,3 +108,35 @@ def test_admission_by_device_memory_budget():
     big.close()
     g.icwf_pool_destroy(small_pool)
     g.icwf_pool_destroy(pool)
+
+
+def test_graph_ticks_equal_eager_ticks_and_launch_once_per_tick():
+    """The same mixed stream with captured tick graphs and with direct launches gives the same
+    results to rounding; with graphs every tick that steps jobs is one graph launch (no job step
+    launched directly), whatever the number of live jobs."""
+    jobs = _jobs()[:4]
+    results = {}
+    for graphs in (True, False):
+        pool = g.icwf_pool_create(1 << 34, 4)
+        g.icwf_pool_set_graphs(pool, graphs)
+        ids = [g.icwf_pool_submit(pool, _make(w, prec, seed).release(), n)
+               for w, prec, seed, n in jobs]
+        for _ in range(100):
+            live, _ = g.icwf_pool_tick(pool)
+            if live == 0 and all(g.icwf_pool_poll(pool, i, w.nx, w.nR)[0] == 2
+                                 for i, (w, *_r) in zip(ids, jobs)):
+                break
+        results[graphs] = [g.icwf_pool_poll(pool, i, w.nx, w.nR)[1] for i, (w, *_r) in zip(ids, jobs)]
+        st = g.icwf_pool_get_stats(pool)
+        if graphs:
+            assert st["eager_job_steps"] == 0
+            assert st["graph_job_steps"] == sum(n for *_r, n in jobs)
+            stepping_ticks = max(n for *_r, n in jobs)
+            assert st["graph_launches"] == stepping_ticks
+            assert st["kernel_nodes"] > 10 * st["graph_job_steps"]
+            assert st["graph_builds"] <= 2 * len(jobs)
+        else:
+            assert st["graph_launches"] == 0 and st["eager_job_steps"] == sum(n for *_r, n in jobs)
+        g.icwf_pool_destroy(pool)
+    for a, b in zip(results[True], results[False]):
+        _same(a, b)
