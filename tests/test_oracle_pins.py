@@ -527,3 +527,24 @@ def test_rk4_with_linear_matrices_matches_fine_integrator():
             C = o.rk4(C, St(k * dt), Ht(k * dt), St((k + 1) * dt), Ht((k + 1) * dt))
         errs.append(np.max(np.abs(C - ref)))
     assert errs[0] < 1e-5 and 12 < errs[0] / errs[1] < 20      # fourth order
+
+
+def test_displaced_coherent_photon_follows_the_classical_oscillator():
+    """The cavity's displaced coherent photon state at lambda = 0 (V separable: atom + w^2 q^2/2,
+    photon mass 1): under the exact solver <q>(t) = q0 cos(w t) + (p0 / w) sin(w t) and the width
+    stays that of the vacuum (a coherent state), to Strang O(dt^2)."""
+    w = cavity(nx=256, x_range=(-40.0, 40.0), nq=128, q_range=(-25.0, 25.0), lam=0.0, n_traj=4,
+               q0=3.0, p0=-0.4)
+    om = w.model["omega"]
+    dt = 0.02
+    ex = Exact2D(w.nx, w.nR, w.x_min, w.x_max, w.R_min, w.R_max, w.mass_x, w.mass_R, dt, w.V)
+    P = w.psi0.copy()
+    q = w.R
+    for n in range(4):
+        rhoq = ex.observables(P)["rho_R"]
+        t = n * 150 * dt
+        mean = w.dR * np.sum(q * rhoq)
+        var = w.dR * np.sum((q - mean) ** 2 * rhoq)
+        assert abs(mean - (3.0 * np.cos(om * t) - 0.4 / om * np.sin(om * t))) < 2e-3
+        assert abs(var - 0.5 / om) < 2e-3 * (0.5 / om)
+        P = ex.run(P, 150)

@@ -174,8 +174,11 @@ def atom_levels(nx, x_range, n=3):
 
 def cavity(nx=2048, x_range=(-80.0, 80.0), nq=256, q_range=(-30.0, 30.0), lam=0.5,
            n_traj=1024, dt=0.01, n_steps=100, n_states=3, svd_rel_cutoff=1e-12,
-           s_reg_eps=1e-4, seed=0, name="cavity") -> Workload:
-    """Electron in a resonant single-mode cavity; Psi0 = phi_1^atom(x) (w/pi)^(1/4) e^{-w q^2/2}.
+           s_reg_eps=1e-4, seed=0, name="cavity", q0=0.0, p0=0.0) -> Workload:
+    """Electron in a resonant single-mode cavity; Psi0 = phi_1^atom(x) times the photon state
+    (w/pi)^(1/4) e^{-w (q - q0)^2 / 2 + i p0 q}: the vacuum for q0 = p0 = 0 (the default), else a
+    coherent state displaced to <q> = q0, <p> = p0 (the displaced coherent photon state of the
+    paper's cavity discussion).
 
     dt = 0.01 a.u.: the product initial state makes every CWF the same, so S starts with rank one
     while the trajectories' pinned potentials differ widely; the regularised coefficient equation
@@ -188,13 +191,13 @@ def cavity(nx=2048, x_range=(-80.0, 80.0), nq=256, q_range=(-30.0, 30.0), lam=0.
     V = cavity_potential(x, q, omega, lam)
     E, phi = bo_states(V, dx, 1.0, n_states=n_states)
     e1 = va[1] * (1.0 if va[1][np.argmax(np.abs(va[1]))] > 0 else -1.0)
-    vac = (omega / math.pi) ** 0.25 * np.exp(-0.5 * omega * q * q)
+    vac = (omega / math.pi) ** 0.25 * np.exp(-0.5 * omega * (q - q0) ** 2 + 1j * p0 * q)
     psi0 = _normalise(np.outer(e1, vac).astype(np.complex128), dx, dq)
     return Workload(name=name, nx=nx, nR=nq, x_min=x_range[0], x_max=x_range[1],
                     R_min=q_range[0], R_max=q_range[1], mass_x=1.0, mass_R=1.0, dt=dt,
                     n_traj=n_traj, n_steps=n_steps, svd_rel_cutoff=svd_rel_cutoff,
                     s_reg_eps=s_reg_eps, seed=seed,
-                    model=dict(kind="cavity", omega=omega, lam=lam), V=V, psi0=psi0,
+                    model=dict(kind="cavity", omega=omega, lam=lam, q0=q0, p0=p0), V=V, psi0=psi0,
                     phi=phi, bo_energies=E)
 
 
