@@ -372,44 +372,54 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(Args args, const __grid_cons
 
 // Planar split operands for one grid side: rows r = (2g + comp) N + b, K index i contiguous:
 // value = comp(psi_b(x_i)) * (g ? u_{g-1}(x_i) : 1), split into hi + lo of the operand type.
+// One CTA per (g, b) row; each thread converts 4 consecutive grid points (16-byte loads of the CWF
+// and the factor, 16-byte (TF32) or 8-byte (BF16) stores per plane).  n is a multiple of 4.
 template <int KIND>
-__global__ void k_prep(const float2* __restrict__ cwf, const double* __restrict__ U, int n, int N,
-                       int G, void* __restrict__ hi_out, void* __restrict__ lo_out) {
-  const size_t total = (size_t)G * N * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n);
-    const size_t gb = e / n;
-    const int b = (int)(gb % N);
-    const int g = (int)(gb / N);
-    const float2 z = cwf[(size_t)b * n + i];
-    const float u = g ? (float)U[(size_t)(g - 1) * n + i] : 1.0f;
-    const float vr = z.x * u, vi = z.y * u;
-    const size_t rp = ((size_t)(2 * g) * N + b) * n + i;
-    const size_t rq = ((size_t)(2 * g + 1) * N + b) * n + i;
-    if (KIND == 0) {
-      __nv_bfloat16* H = (__nv_bfloat16*)hi_out;
-      __nv_bfloat16* L = (__nv_bfloat16*)lo_out;
-      const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hq = __float2bfloat16_rn(vi);
-      H[rp] = hr;
-      L[rp] = __float2bfloat16_rn(vr - __bfloat162float(hr));
-      H[rq] = hq;
-      L[rq] = __float2bfloat16_rn(vi - __bfloat162float(hq));
-    } else {
-      // TF32: keep the top 10 mantissa bits (round to nearest), the remainder as the low piece
-      float* H = (float*)hi_out;
-      float* L = (float*)lo_out;
-      auto r19 = [](float v) {
-        uint32_t u32 = __float_as_uint(v);
-        u32 = (u32 + 0x1000u) & 0xFFFFE000u;
-        return __uint_as_float(u32);
-      };
-      const float hr = r19(vr), hq = r19(vi);
-      H[rp] = hr;
-      L[rp] = r19(vr - hr);
-      H[rq] = hq;
-      L[rq] = r19(vi - hq);
+__device__ __forceinline__ void split4(const float (&v)[4], void* hi_out, void* lo_out, size_t at) {
+  if (KIND == 0) {
+    __nv_bfloat16 h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = __float2bfloat16_rn(v[e]);
+      l[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
     }
+    *(uint2*)((__nv_bfloat16*)hi_out + at) = *(const uint2*)h;
+    *(uint2*)((__nv_bfloat16*)lo_out + at) = *(const uint2*)l;
+  } else {
+    // TF32: keep the top 10 mantissa bits (round to nearest), the remainder as the low piece
+    auto r19 = [](float x) {
+      uint32_t u32 = __float_as_uint(x);
+      u32 = (u32 + 0x1000u) & 0xFFFFE000u;
+      return __uint_as_float(u32);
+    };
+    float4 h, l;
+    h.x = r19(v[0]); h.y = r19(v[1]); h.z = r19(v[2]); h.w = r19(v[3]);
+    l.x = r19(v[0] - h.x); l.y = r19(v[1] - h.y); l.z = r19(v[2] - h.z); l.w = r19(v[3] - h.w);
+    *(float4*)((float*)hi_out + at) = h;
+    *(float4*)((float*)lo_out + at) = l;
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_prep(const float2* __restrict__ cwf,
+                                              const double* __restrict__ U, int n, int N,
+                                              void* __restrict__ hi_out, void* __restrict__ lo_out) {
+  const int row = blockIdx.x;             // g * N + b
+  const int g = row / N, b = row - g * N;
+  const float4* src = (const float4*)(cwf + (size_t)b * n);        // 2 complex per float4
+  const double2* u = g ? (const double2*)(U + (size_t)(g - 1) * n) : nullptr;
+  const size_t rp = ((size_t)(2 * g) * N + b) * n, rq = ((size_t)(2 * g + 1) * N + b) * n;
+  for (int i4 = threadIdx.x; 4 * i4 < n; i4 += blockDim.x) {
+    const float4 z01 = src[2 * i4], z23 = src[2 * i4 + 1];
+    float f[4] = {1.f, 1.f, 1.f, 1.f};
+    if (u) {
+      const double2 u01 = u[2 * i4], u23 = u[2 * i4 + 1];
+      f[0] = (float)u01.x; f[1] = (float)u01.y; f[2] = (float)u23.x; f[3] = (float)u23.y;
+    }
+    const float vr[4] = {z01.x * f[0], z01.z * f[1], z23.x * f[2], z23.z * f[3]};
+    const float vi[4] = {z01.y * f[0], z01.w * f[1], z23.y * f[2], z23.w * f[3]};
+    split4<KIND>(vr, hi_out, lo_out, rp + 4 * (size_t)i4);
+    split4<KIND>(vi, hi_out, lo_out, rq + 4 * (size_t)i4);
   }
 }
 
@@ -450,15 +460,14 @@ bool launch_assemble_tc(const JobView& j, int precision, bool exact_s, double2* 
   void* xlo = p; p += al(nxe);
   void* Rhi = p; p += al(nRe);
   void* Rlo = p; p += al(nRe);
-  const int threads = 256;
-  auto grid_for = [&](size_t n) { size_t g = (n + threads - 1) / threads; return (unsigned)(g > 8192 ? 8192 : g); };
-  const size_t totx = (size_t)G * j.N * j.nx, totR = (size_t)G * j.N * j.nR;
+  const unsigned rows = (unsigned)(G * j.N);
+  const int tx = j.nx / 4 < 256 ? j.nx / 4 : 256, tR = j.nR / 4 < 256 ? j.nR / 4 : 256;
   if (kind) {
-    k_prep<1><<<grid_for(totx), threads, 0, s>>>((const float2*)j.psi, j.U, j.nx, j.N, G, xhi, xlo);
-    k_prep<1><<<grid_for(totR), threads, 0, s>>>((const float2*)j.chi, j.W, j.nR, j.N, G, Rhi, Rlo);
+    k_prep<1><<<rows, tx, 0, s>>>((const float2*)j.psi, j.U, j.nx, j.N, xhi, xlo);
+    k_prep<1><<<rows, tR, 0, s>>>((const float2*)j.chi, j.W, j.nR, j.N, Rhi, Rlo);
   } else {
-    k_prep<0><<<grid_for(totx), threads, 0, s>>>((const float2*)j.psi, j.U, j.nx, j.N, G, xhi, xlo);
-    k_prep<0><<<grid_for(totR), threads, 0, s>>>((const float2*)j.chi, j.W, j.nR, j.N, G, Rhi, Rlo);
+    k_prep<0><<<rows, tx, 0, s>>>((const float2*)j.psi, j.U, j.nx, j.N, xhi, xlo);
+    k_prep<0><<<rows, tR, 0, s>>>((const float2*)j.chi, j.W, j.nR, j.N, Rhi, Rlo);
   }
   Maps m;
   bool ok = make_map(&m.xhi_a, xhi, kind, j.nx, rx, BM) && make_map(&m.xlo_a, xlo, kind, j.nx, rx, BM) &&

@@ -455,6 +455,11 @@ __global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb,
   const int jp = li, jb = li - 1;
   unsigned* diag = ctl + (T + 2) + 2 * li;     // [li][matrix]: finished quadrants
   unsigned* pdone = ctl + 3 * (T + 2) + 2 * li;  // [li][matrix]: diagonal factor published
+  // programmatic dependent launch: the next block column's launch may become resident now; this
+  // launch reads nothing of the previous one's output before griddepcontrol.wait, which returns
+  // once the previous launch has completed and its writes are visible
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (threadIdx.x == 0) s_t = atomicAdd(ctl + li, 1u);
   __syncthreads();
   int t = (int)s_t;
@@ -1105,6 +1110,12 @@ int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, 
     attr = true;
   }
   cudaMemsetAsync(ctl, 0, chol_ctl_words(N) * sizeof(unsigned), s);
+  // launches 1.. are programmatic dependents of the previous one (the kernel waits on
+  // griddepcontrol before touching data), so a launch's CTAs are resident when its predecessor
+  // ends instead of paying the launch latency on the factorisation's critical path
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
   for (int li = 0; li <= T; ++li) {
     const int jb = li - 1;
     const int rt = T - jb - 2;
@@ -1112,7 +1123,14 @@ int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, 
     const int rows = N - (li + 1) * NB;
     const int nslab = (li < T && rows > 0) ? (rows + TS_ROWS - 1) / TS_ROWS : 0;
     const int per = (jb >= 0 && li < T ? 3 : 0) + (li < T ? 1 : 0) + (li >= 1 ? 1 : 0) + nherk + nslab;
-    k_chol_step_df<<<nbatch * per, CS_THREADS, CS_SMEM_LAUNCH, s>>>(N, mb, nbatch, li, ctl, status);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nbatch * per);
+    cfg.blockDim = dim3(CS_THREADS);
+    cfg.dynamicSmemBytes = CS_SMEM_LAUNCH;
+    cfg.stream = s;
+    cfg.attrs = pdl;
+    cfg.numAttrs = li > 0 ? 1 : 0;   // the first launch follows the memset in stream order
+    cudaLaunchKernelEx(&cfg, k_chol_step_df, N, mb, nbatch, li, ctl, status);
   }
   return T + 2;
 }
