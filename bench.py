@@ -42,8 +42,9 @@ DF64_CMAC_OPS = 39
 DF64_TFLOPS = FP32_LANE_OPS * 8 / DF64_CMAC_OPS / 1e12
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
 # DRAM bytes (read + write) per family call from one ncu capture, with the profile that gives them;
-# keyed by (family, mode, N).  Valid only while the kernels are the ones profiled.
-TRAFFIC = {("cholesky", "tf32x3", 1024): (193.4e6, "profiles/k_chol_step_df_mixed_N1024.md")}
+# keyed by (family, mode, N).  Valid only while the kernels are the ones profiled (the Cholesky's
+# capture predates its programmatic-dependent launches, so none is kept).
+TRAFFIC = {}
 
 
 def parse():
@@ -397,7 +398,7 @@ def run_ours(args, rank, ws, local):
         out["vs_exact"] = run_vs_exact(w, prec, args.vs_exact, args.vs_exact_every, w.seed,
                                        int(args.overlap_split))
     if rank == 0 and args.serving_jobs > 0:
-        out["serving"] = run_serving(args.serving_jobs)
+        out["serving"] = run_serving(args.serving_jobs, args.mode if args.mode != "fp64" else "tf32x3")
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(w, args.cpu_budget_s)
     return out
@@ -621,13 +622,15 @@ def run_cavity_line(args, local, peaks, steps=50, warmup=3):
 
 def _model_library(rng):
     """A few synthetic model instances (grids and parameters drawn like the mixed-size stream:
-    Shin-Metiu with R_f ~ U[4, 6], R0 ~ U[-5, -3]; cavity with lambda ~ U[0.1, 1])."""
+    Shin-Metiu with R_f ~ U[4, 6], R0 ~ U[-5, -3]; cavity with lambda ~ U[0.1, 1]).  Shin-Metiu
+    runs at dt 0.05 with eps 1e-6, the cavity at dt 0.01 with eps 1e-4 (its product initial state
+    makes the coefficient equation stiff)."""
     from workloads import cavity, shin_metiu
     lib = []
     for nx, nR in ((256, 128), (512, 128), (512, 256)):
         lib.append(shin_metiu(nx=nx, x_range=(-60.0, 60.0), nR=nR, R_range=(-9.0, 9.0),
                               Rf=float(rng.uniform(4, 6)), R0=float(rng.uniform(-5, -3)),
-                              dt=0.05, n_traj=64, svd_rel_cutoff=1e-8, s_reg_eps=1e-4))
+                              dt=0.05, n_traj=64, svd_rel_cutoff=1e-8, s_reg_eps=1e-6))
     for nx, nq in ((512, 128), (1024, 128)):
         lib.append(cavity(nx=nx, x_range=(-60.0, 60.0), nq=nq, q_range=(-20.0, 20.0),
                           lam=float(rng.uniform(0.1, 1.0)), dt=0.01, n_traj=64,
@@ -635,47 +638,40 @@ def _model_library(rng):
     return lib
 
 
-def run_serving(n_jobs, seed=0, load=0.7, max_live=16):
-    """Poisson stream of mixed-size jobs through the pool (continuous batching): job latency
-    p50/p99 (arrival -> result on the host) and aggregate trajectory-steps/s."""
+def _serving_jobs(n_jobs, seed):
     import numpy as np
-    import paper_1805_11169_gb300 as g
     rng = np.random.default_rng(seed)
     lib = _model_library(rng)
-    Ns = (64, 128, 256, 512)
-    jobs = []
-    for j in range(n_jobs):
-        jobs.append(dict(model=int(rng.integers(len(lib))), N=int(rng.choice(Ns)),
-                         steps=int(rng.integers(100, 401)), seed=int(rng.integers(1 << 31))))
+    Ns = (64, 128, 256, 512, 1024, 2048)
+    jobs = [dict(model=int(rng.integers(len(lib))), N=int(rng.choice(Ns)),
+                 steps=int(rng.integers(100, 401)), seed=int(rng.integers(1 << 31)))
+            for _ in range(n_jobs)]
+    return lib, jobs
 
-    def make(job):
-        w = lib[job["model"]].with_(n_traj=job["N"])
-        sim = g.Icwf(g.params_from(w, precision=2), w.V)
-        sim.set_projectors(w.phi)
-        sim.init_from_density(w.psi0, job["seed"])
-        return sim, w
 
-    # isolated service time of the mean job (calibrates the arrival rate to the load factor)
-    t_iso = []
-    for job in jobs[: min(4, n_jobs)]:
-        t0 = time.perf_counter()
-        sim, _ = make(job)
-        sim.step(job["steps"])
-        sim.observables()
-        sim.close()
-        t_iso.append((time.perf_counter() - t0) / job["steps"])
-    mean_service = float(np.mean(t_iso)) * float(np.mean([j["steps"] for j in jobs]))
-    rate = load * max(1.0, max_live / 4) / mean_service
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
+def _make_job(lib, job, precision):
+    import paper_1805_11169_gb300 as g
+    w = lib[job["model"]].with_(n_traj=job["N"])
+    sim = g.Icwf(g.params_from(w, precision=precision), w.V)
+    sim.set_projectors(w.phi)
+    sim.init_from_density(w.psi0, job["seed"])
+    return sim, w
 
+
+def _run_stream(lib, jobs, arrivals, graphs, max_live, precision):
+    """Feed the jobs at their arrival times into a pool and tick it until all are done."""
+    import numpy as np
+    import paper_1805_11169_gb300 as g
+    n_jobs = len(jobs)
     pool = g.icwf_pool_create(64 << 30, max_live)
+    g.icwf_pool_set_graphs(pool, graphs)
     t_start = time.perf_counter()
-    submitted, lat, ids, grids = 0, {}, {}, {}
+    submitted, lat, ids, grids, results = 0, {}, {}, {}, {}
     done = set()
     while len(done) < n_jobs:
         now = time.perf_counter() - t_start
         while submitted < n_jobs and arrivals[submitted] <= now:
-            sim, w = make(jobs[submitted])
+            sim, w = _make_job(lib, jobs[submitted], precision)
             ids[submitted] = g.icwf_pool_submit(pool, sim.release(), jobs[submitted]["steps"])
             grids[submitted] = (w.nx, w.nR)
             submitted += 1
@@ -686,19 +682,77 @@ def run_serving(n_jobs, seed=0, load=0.7, max_live=16):
         for j, jid in ids.items():
             if j in done:
                 continue
-            st, _ = g.icwf_pool_poll(pool, jid, *grids[j])
+            st, obs = g.icwf_pool_poll(pool, jid, *grids[j])
             if st in (2, 3):
                 done.add(j)
                 lat[j] = time.perf_counter() - t_start - arrivals[j]
+                results[j] = obs if st == 2 else None
     makespan = time.perf_counter() - t_start
+    stats = g.icwf_pool_get_stats(pool)
     g.icwf_pool_destroy(pool)
     L = np.array([lat[j] for j in range(n_jobs)])
     ts = sum(j["N"] * j["steps"] for j in jobs)
-    return {"jobs": n_jobs, "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)),
+    stepping_ticks = max(1, stats["graph_launches"] + (stats["ticks"] if not graphs else 0))
+    return {"p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)),
             "traj_steps_per_s": ts / makespan, "makespan_s": makespan,
-            "arrival_rate_per_s": rate, "max_live": max_live, "precision": "mixed-tf32x3",
-            "stream": "Poisson arrivals; Shin-Metiu (3 grids) and cavity (2 grids) models; "
-                      "N in {64,128,256,512}; 100-400 steps; CI-sized stand-in for 2000 jobs"}
+            "failed": sum(1 for r in results.values() if r is None),
+            "ticks": stats["ticks"], "graph_launches": stats["graph_launches"],
+            "graph_builds": stats["graph_builds"],
+            "kernels_per_graph_launch": (stats["kernel_nodes"] / stats["graph_launches"]
+                                         if stats["graph_launches"] else None),
+            "host_launches_per_tick": (stats["graph_launches"] / stats["ticks"] if graphs else
+                                       None),
+            "eager_job_steps": stats["eager_job_steps"]}, results
+
+
+def run_serving(n_jobs, mode="tf32x3", seed=0, load=0.7, max_live=16, n_checked=4):
+    """Poisson stream of mixed-size jobs (N up to 2048) through the pool (continuous batching),
+    once with captured tick graphs (the default) and once with direct launches: job latency
+    p50/p99 (arrival -> result on the host), aggregate trajectory-steps/s and launches per tick.
+    Jobs' mixed-precision results are checked against FP64 runs of the same jobs (a sample of the
+    small ones: the FP64 path is ~50x slower)."""
+    import numpy as np
+    prec = MODES[mode][0]
+    lib, jobs = _serving_jobs(n_jobs, seed)
+    # isolated service time of the mean job: the arrival rate is `load` times the rate at which
+    # the GPU serves jobs one at a time
+    t_iso = []
+    for job in jobs[: min(4, n_jobs)]:
+        t0 = time.perf_counter()
+        sim, _ = _make_job(lib, job, prec)
+        sim.step(job["steps"])
+        sim.observables()
+        sim.close()
+        t_iso.append((time.perf_counter() - t0) / job["steps"] / job["N"])
+    mean_service = float(np.mean(t_iso)) * float(np.mean([j["steps"] * j["N"] for j in jobs]))
+    rate = load / mean_service
+    arrivals = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / rate, n_jobs))
+    graphs, res = _run_stream(lib, jobs, arrivals, True, max_live, prec)
+    eager, _ = _run_stream(lib, jobs, arrivals, False, max_live, prec)
+    # precision check: the first n_checked jobs with N <= 256, in FP64, same seed, alone
+    checks = []
+    for j, job in enumerate(jobs):
+        if len(checks) >= n_checked:
+            break
+        if job["N"] > 256 or res.get(j) is None:
+            continue
+        sim, w = _make_job(lib, job, 0)
+        sim.step(job["steps"])
+        ref = sim.observables()
+        sim.close()
+        ob = res[j]
+        checks.append({"job": j, "model": lib[job["model"]].model["kind"], "N": job["N"],
+                       "steps": job["steps"],
+                       "rho_x_L1": float(w.dx * np.sum(np.abs(ob["rho_x"] - ref["rho_x"]))),
+                       "rho_R_L1": float(w.dR * np.sum(np.abs(ob["rho_R"] - ref["rho_R"]))),
+                       "pop_L1": float(np.sum(np.abs(ob["pop"] - ref["pop"])))})
+    return {"jobs": n_jobs, "p50_s": graphs["p50_s"], "p99_s": graphs["p99_s"],
+            "traj_steps_per_s": graphs["traj_steps_per_s"], "graphs": graphs, "eager": eager,
+            "arrival_rate_per_s": rate, "max_live": max_live, "precision": MODES[mode][1],
+            "vs_fp64": checks,
+            "stream": "Poisson arrivals; Shin-Metiu (3 grids, dt 0.05, eps 1e-6) and cavity "
+                      "(2 grids, dt 0.01, eps 1e-4) models; N in {64..2048}; 100-400 steps; "
+                      "CI-sized stand-in for 2000 jobs"}
 
 
 # ---------------------------------------------------------------- reference arm (the oracle)
