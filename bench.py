@@ -79,6 +79,9 @@ def parse():
                     help="Shin-Metiu 1024 x 512 (default) or the cavity 2048 x 256")
     ap.add_argument("--lam", type=float, default=0.5, help="cavity coupling lambda")
     ap.add_argument("--eps", type=float, default=None, help="override the mode's regulariser")
+    ap.add_argument("--workload-cache", default=None, metavar="NPZ",
+                    help="read the Shin-Metiu tables (V, Psi0, BO states) from this file if it "
+                         "holds the grid, else build and save them (for profiling runs)")
     ap.add_argument("--overlap-split", action="store_true",
                     help="mixed modes: S from the split products (FP32 accumulation) instead of "
                          "the exact fixed-point Gram")
@@ -91,6 +94,36 @@ _WORKLOADS = {}
 
 
 CAVITY_EPS = 1e-4   # the cavity's regulariser in every mode (its coefficient equation is stiff)
+_CACHE = None       # --workload-cache: .npz file the Shin-Metiu tables are read from / saved to
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    sys.stderr.write("[bench %.1fs] %s\n" % (time.perf_counter() - _T0, msg))
+    sys.stderr.flush()
+
+
+def _sm_paper_cached(nx, nR):
+    """The Shin-Metiu paper-scale workload, its tables (V, Psi0, BO states) read from the cache
+    file when it holds this grid, else built (and saved there)."""
+    import dataclasses
+    import numpy as np
+    import workloads
+    tag = np.array([nx, nR])
+    if os.path.exists(_CACHE):
+        z = np.load(_CACHE, allow_pickle=False)
+        if np.array_equal(z["grid"], tag):
+            fields = {k: (z[k].item() if z[k].ndim == 0 else z[k]) for k in z.files
+                      if k not in ("grid", "model_keys", "model_vals")}
+            model = dict(zip(z["model_keys"].tolist(), z["model_vals"].tolist()))
+            model["kind"] = "shin_metiu"
+            return workloads.Workload(model=model, **fields)
+    w = workloads.WORKLOADS["sm_paper"](nx=nx, nR=nR)
+    d = {f.name: getattr(w, f.name) for f in dataclasses.fields(w) if f.name != "model"}
+    mk = [k for k in w.model if k != "kind"]
+    np.savez(_CACHE, grid=tag, model_keys=np.array(mk),
+             model_vals=np.array([float(w.model[k]) for k in mk]), **d)
+    return w
 
 
 def make_workload(n_traj, cutoff, eps, nx=1024, nR=512, kind="shin_metiu", lam=0.5):
@@ -101,8 +134,11 @@ def make_workload(n_traj, cutoff, eps, nx=1024, nR=512, kind="shin_metiu", lam=0
     if key not in _WORKLOADS:
         if kind == "cavity":
             _WORKLOADS[key] = WORKLOADS["cavity"](lam=lam)
+        elif _CACHE:
+            _WORKLOADS[key] = _sm_paper_cached(nx, nR)
         else:
             _WORKLOADS[key] = WORKLOADS["sm_paper"](nx=nx, nR=nR)
+        log(f"workload {kind} {nx}x{nR} ready")
     if kind == "cavity":
         eps = max(eps, CAVITY_EPS)
     return _WORKLOADS[key].with_(n_traj=n_traj, svd_rel_cutoff=cutoff, s_reg_eps=eps)
@@ -342,7 +378,9 @@ def run_ours(args, rank, ws, local):
     sim.set_projectors(w.phi)
     sim.init_from_density(w.psi0, w.seed)
     info = sim.info()
+    log("handle created and initialised")
     total_ms, prof, launches, clocks, n_obs = timed_steps(sim, args.steps, args.warmup, local, ws)
+    log("timed steps done")
     total_s = max_over_ranks(total_ms / 1e3, ws)
     value = whole_job_rate(ws, w.n_traj * args.steps, total_s)
     sim.close()
@@ -801,7 +839,9 @@ def run_reference(args, rank, ws):
 
 
 def main():
+    global _CACHE
     args = parse()
+    _CACHE = args.workload_cache
     rank, ws, local = dist_init()
     if args.impl == "reference":
         out = run_reference(args, rank, ws)

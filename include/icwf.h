@@ -174,6 +174,23 @@ icwf_status icwf_get_matrices(icwf_handle h, double* S, double* H, double* Heff)
 
 icwf_status icwf_get_info(icwf_handle h, icwf_info* out);
 
+/* --- checkpoint / resume ------------------------------------------------------------------- */
+
+/* Bytes of the handle's time-stepping state as icwf_save_state writes it: a header (sizes,
+ * precision, step count, time) and the device state at the current time (CWFs in their storage
+ * precision, positions, pinned factor values, C, S, Heff, the Cholesky factor of S + eps I with
+ * its inverted diagonal blocks, the clamp counter). */
+icwf_status icwf_state_bytes(icwf_handle h, size_t* bytes);
+
+/* Copy the state into buf (host, caller-owned, at least icwf_state_bytes bytes). */
+icwf_status icwf_save_state(icwf_handle h, void* buf, size_t bytes);
+
+/* Restore a state saved by icwf_save_state from a handle created with the same parameters and
+ * the same V (sizes, rank, precision, scheme and solver are checked, else ICWF_ERR_ARG); the handle
+ * is then initialised and continues bit for bit as the saved handle would have.  Projectors are
+ * not part of the state. */
+icwf_status icwf_load_state(icwf_handle h, const void* buf, size_t bytes);
+
 /* Columns of Heff = W - W1 - W2 (Eq. W, W1, W2) by the full double sum over the grid, without the
  * rank-k factorisation of V:
  *   Heff[a, b] = dx dR sum_ij conj(psi_a(x_i) chi_a(R_j)) [V(x_i,R_j) - V(x_i,R_b) - V(x_b,R_j)]

@@ -79,6 +79,9 @@ def _load():
         "icwf_get_matrices": [H, d, d, d],
         "icwf_get_info": [H, P(icwf_info)],
         "icwf_heff_direct": [H, ct.c_int32, P(ct.c_int32), d],
+        "icwf_state_bytes": [H, P(ct.c_size_t)],
+        "icwf_save_state": [H, ct.c_void_p, ct.c_size_t],
+        "icwf_load_state": [H, ct.c_void_p, ct.c_size_t],
         "icwf_get_stream": [H, P(ct.c_void_p)],
         "icwf_set_regularisation": [H, ct.c_double],
         "icwf_set_wait_limit": [H, ct.c_int64],
@@ -246,6 +249,19 @@ def icwf_heff_direct(h, N: int, cols) -> np.ndarray:
     return out.T.copy()
 
 
+def icwf_save_state(h) -> bytes:
+    n = ct.c_size_t()
+    _check(LIB.icwf_state_bytes(h, ct.byref(n)), h)
+    buf = ct.create_string_buffer(n.value)
+    _check(LIB.icwf_save_state(h, buf, n.value), h)
+    return buf.raw
+
+
+def icwf_load_state(h, blob: bytes):
+    buf = ct.create_string_buffer(blob, len(blob))
+    _check(LIB.icwf_load_state(h, buf, len(blob)), h)
+
+
 def icwf_get_stream(h) -> int:
     s = ct.c_void_p()
     _check(LIB.icwf_get_stream(h, ct.byref(s)), h)
@@ -376,6 +392,12 @@ class Icwf:
 
     def info(self):
         return icwf_get_info(self.h)
+
+    def save_state(self) -> bytes:
+        return icwf_save_state(self.h)
+
+    def load_state(self, blob: bytes):
+        icwf_load_state(self.h, blob)
 
     def heff_direct(self, cols):
         return icwf_heff_direct(self.h, self.p.n_traj, cols)

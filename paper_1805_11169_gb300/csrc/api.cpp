@@ -6,6 +6,7 @@
 // written (the sampler must reproduce the published SplitMix64 stream and the inverse-CDF draw
 // bit for bit on every host architecture).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -31,6 +32,12 @@ using namespace icwf;
 namespace {
 
 thread_local std::string g_err;   // last failure without a handle
+
+// NVTX range around a public call (visible in Nsight timelines; no cost without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 enum Fam {
   F_VELOCITY, F_PROPAGATE, F_ASSEMBLE, F_SHIFT, F_POTRF, F_MATVEC, F_SOLVE, F_RK4, F_OBS,
@@ -899,6 +906,7 @@ icwf_status icwf_init_from_positions(icwf_handle h, const double* psi0, const do
 }
 
 icwf_status icwf_init_from_density(icwf_handle h, const double* psi0, uint64_t seed) {
+  NvtxRange nvtx_("icwf_init_from_density");
   if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_init_from_density: NULL handle");
   if (!psi0) return fail(h, ICWF_ERR_ARG, "icwf_init_from_density: psi0 is NULL");
   const int nx = h->nx, nR = h->nR, N = h->N;
@@ -932,6 +940,7 @@ icwf_status icwf_init_from_density(icwf_handle h, const double* psi0, uint64_t s
 }
 
 icwf_status icwf_step(icwf_handle h, int32_t n_steps) {
+  NvtxRange nvtx_("icwf_step");
   if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_step: NULL handle");
   if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_step: handle not initialised");
   if (n_steps < 0) return fail(h, ICWF_ERR_ARG, "icwf_step: n_steps < 0");
@@ -941,6 +950,7 @@ icwf_status icwf_step(icwf_handle h, int32_t n_steps) {
 }
 
 icwf_status icwf_observables(icwf_handle h, icwf_obs* out) {
+  NvtxRange nvtx_("icwf_observables");
   if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_observables: NULL handle");
   if (!out) return fail(h, ICWF_ERR_ARG, "icwf_observables: out is NULL");
   if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_observables: handle not initialised");
@@ -1056,6 +1066,92 @@ icwf_status icwf_get_matrices(icwf_handle h, double* S, double* Hout, double* He
   cudaStreamSynchronize(s);
   cudaFree(tmp);
   if (e != cudaSuccess) return fail(h, ICWF_ERR_CUDA, "icwf_get_matrices: copy failed");
+  return ICWF_OK;
+}
+
+// ---- checkpoint / resume ----------------------------------------------------------------------
+
+namespace {
+
+struct StateHeader {
+  char magic[8];          // "ICWFSTA1"
+  int32_t version, N, nx, nR, K, precision, coeff_scheme, df_solve, cwf_elem, cur;
+  int64_t steps;
+  double t;
+};
+
+// Device regions that make up the time-stepping state at the current time (in this order).
+std::vector<std::pair<void*, size_t>> state_regions(icwf_ctx* h) {
+  const size_t N = h->N, NN = N * N, K = h->K, cw = h->cwf_elem;
+  const int c = h->cur;
+  return {{h->psi, N * h->nx * cw}, {h->chi, N * h->nR * cw},
+          {h->x, N * 8}, {h->R, N * 8}, {h->xo, N * 8}, {h->Ro, N * 8},
+          {h->px, K * N * 8}, {h->pR, K * N * 8}, {h->dvec, N * 8},
+          {h->C, N * 16}, {h->S[c], NN * 16}, {h->H[c], NN * 16}, {h->L[c], NN * 16},
+          {h->invL[c], N * 8}, {h->DL[c], N * 512}, {h->status + STATUS_CLAMPED, 4}};
+}
+
+size_t state_bytes(icwf_ctx* h) {
+  size_t b = sizeof(StateHeader);
+  for (auto& r : state_regions(h)) b += r.second;
+  return b;
+}
+
+}  // namespace
+
+icwf_status icwf_state_bytes(icwf_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(h, ICWF_ERR_ARG, "icwf_state_bytes: NULL argument");
+  *bytes = state_bytes(h);
+  return ICWF_OK;
+}
+
+icwf_status icwf_save_state(icwf_handle h, void* buf, size_t bytes) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_save_state: NULL handle");
+  NvtxRange nvtx_("icwf_save_state");
+  if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_save_state: handle not initialised");
+  if (!buf || bytes < state_bytes(h))
+    return fail(h, ICWF_ERR_ARG, "icwf_save_state: buffer smaller than icwf_state_bytes");
+  StateHeader hd{};
+  std::memcpy(hd.magic, "ICWFSTA1", 8);
+  hd.version = 1; hd.N = h->N; hd.nx = h->nx; hd.nR = h->nR; hd.K = h->K;
+  hd.precision = h->p.precision; hd.coeff_scheme = h->p.coeff_scheme; hd.df_solve = h->df_solve;
+  hd.cwf_elem = (int)h->cwf_elem; hd.cur = h->cur; hd.steps = h->steps; hd.t = h->t;
+  CK(cudaStreamSynchronize(h->stream));
+  char* p = (char*)buf;
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  for (auto& r : state_regions(h)) {
+    CK(cudaMemcpy(p, r.first, r.second, cudaMemcpyDeviceToHost));
+    p += r.second;
+  }
+  return ICWF_OK;
+}
+
+icwf_status icwf_load_state(icwf_handle h, const void* buf, size_t bytes) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_load_state: NULL handle");
+  NvtxRange nvtx_("icwf_load_state");
+  if (!buf || bytes < sizeof(StateHeader)) return fail(h, ICWF_ERR_ARG, "icwf_load_state: buffer too small");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "ICWFSTA1", 8) != 0 || hd.version != 1)
+    return fail(h, ICWF_ERR_ARG, "icwf_load_state: not a saved ICWF state");
+  if (hd.N != h->N || hd.nx != h->nx || hd.nR != h->nR || hd.K != h->K ||
+      hd.precision != h->p.precision || hd.coeff_scheme != h->p.coeff_scheme ||
+      hd.df_solve != (int)h->df_solve || hd.cwf_elem != (int)h->cwf_elem)
+    return fail(h, ICWF_ERR_ARG, "icwf_load_state: state saved from a handle with other parameters");
+  CK(cudaStreamSynchronize(h->stream));
+  h->cur = hd.cur;
+  if (bytes < state_bytes(h)) return fail(h, ICWF_ERR_ARG, "icwf_load_state: buffer too small");
+  const char* p = (const char*)buf + sizeof(hd);
+  for (auto& r : state_regions(h)) {
+    CK(cudaMemcpy(r.first, p, r.second, cudaMemcpyHostToDevice));
+    p += r.second;
+  }
+  const int flags0 = 0;
+  CK(cudaMemcpy(h->status + STATUS_FLAGS, &flags0, sizeof(int), cudaMemcpyHostToDevice));
+  h->steps = hd.steps;
+  h->t = hd.t;
+  h->initialised = true;
   return ICWF_OK;
 }
 
@@ -1291,6 +1387,7 @@ static void finish_job(icwf_pool pool, int id, bool ok) {
 // the jobs share nothing, so their kernels overlap freely.  Without graphs (or if a capture
 // fails) every job's kernels are launched directly on its own streams.
 icwf_status icwf_pool_tick(icwf_pool pool, int32_t* n_live, int32_t* n_finished) {
+  NvtxRange nvtx_("icwf_pool_tick");
   if (!pool) return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_tick: NULL pool");
   while (!pool->pending.empty() && (int)pool->live.size() < pool->max_jobs) {
     const int id = pool->pending.front();
