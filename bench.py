@@ -79,6 +79,8 @@ def parse():
                     help="Shin-Metiu 1024 x 512 (default) or the cavity 2048 x 256")
     ap.add_argument("--lam", type=float, default=0.5, help="cavity coupling lambda")
     ap.add_argument("--eps", type=float, default=None, help="override the mode's regulariser")
+    ap.add_argument("--no-step-graphs", action="store_true",
+                    help="launch the step's kernels directly instead of replaying captured graphs")
     ap.add_argument("--workload-cache", default=None, metavar="NPZ",
                     help="read the Shin-Metiu tables (V, Psi0, BO states) from this file if it "
                          "holds the grid, else build and save them (for profiling runs)")
@@ -314,18 +316,18 @@ def n_obs_calls(steps):
     return max(1, steps // OBS_EVERY)
 
 
-def timed_steps(sim, steps, warmup, local, ws=1):
+def timed_steps(sim, steps, warmup, local, ws=1, prof_steps=20):
     """W untimed steps, then `steps` steps timed one by one with CUDA events on the library's
     stream (L2 flushed before each), observables n_obs_calls(steps) times inside the timed
-    region; per-family kernel times from the library's own events; clocks sampled meanwhile."""
+    region, clocks sampled meanwhile.  The library replays each step as a captured CUDA graph
+    there; the per-family kernel times come from a separate pass of `prof_steps` steps with the
+    library's timing events on (direct launches)."""
     import torch
     import paper_1805_11169_gb300 as g
     stream = torch.cuda.ExternalStream(sim.stream())
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     for _ in range(warmup):
         sim.step(1)
-    g.icwf_profile_reset(sim.h)
-    g.icwf_profile_enable(sim.h, True)
     launches0 = sim.info()["kernel_launches"]
     n_obs = n_obs_calls(steps)
     obs_at = {steps - 1 - k * (steps // n_obs) for k in range(n_obs)}
@@ -347,9 +349,19 @@ def timed_steps(sim, steps, warmup, local, ws=1):
             step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     barrier(ws)
-    g.icwf_profile_enable(sim.h, False)
-    prof = g.icwf_profile_read(sim.h)
     launches = sim.info()["kernel_launches"] - launches0 + 4 * n_obs
+    # per-family breakdown (direct launches, timing events on), scaled to per-step values below
+    g.icwf_profile_reset(sim.h)
+    g.icwf_profile_enable(sim.h, True)
+    for s in range(prof_steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        sim.step(1)
+    sim.observables()
+    g.icwf_profile_enable(sim.h, False)
+    raw = g.icwf_profile_read(sim.h)
+    prof = {f: (ms * steps / prof_steps, int(round(n * steps / prof_steps))) for f, (ms, n) in raw.items()}
+    prof["observables"] = (raw["observables"][0] * n_obs, raw["observables"][1] * n_obs)
     return sum(step_ms), prof, launches, clk.summary(), n_obs
 
 
@@ -377,6 +389,8 @@ def run_ours(args, rank, ws, local):
     sim = g.Icwf(params, w.V)
     sim.set_projectors(w.phi)
     sim.init_from_density(w.psi0, w.seed)
+    if args.no_step_graphs:
+        sim.set_step_graphs(False)
     info = sim.info()
     log("handle created and initialised")
     total_ms, prof, launches, clocks, n_obs = timed_steps(sim, args.steps, args.warmup, local, ws)
@@ -413,6 +427,8 @@ def run_ours(args, rank, ws, local):
                    "solve": ("fp64" if args.mode == "fp64" or args.solve == "fp64"
                              else "double-float (FP32 pairs)"),
                    "obs_every": OBS_EVERY, "obs_calls_timed": n_obs,
+                   "step_launch": ("direct kernel launches" if args.no_step_graphs else
+                                   "one captured CUDA graph per step"),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": rl,

@@ -208,6 +208,12 @@ icwf_status icwf_heff_direct(icwf_handle h, int32_t n_cols, const int32_t* cols,
  * fails and returns ICWF_ERR_NUMERIC (the failure path the tests drive on purpose). */
 icwf_status icwf_set_regularisation(icwf_handle h, double eps);
 
+/* icwf_step replays each time step as a captured CUDA graph (recorded on the first call, one
+ * graph per parity of the ping-pong matrix buffers; re-recorded after icwf_set_regularisation)
+ * unless per-kernel timing (icwf_profile_enable) is on.  on = 0 launches the step's kernels
+ * directly instead; on = 1 (default) uses the graphs. */
+icwf_status icwf_set_step_graphs(icwf_handle h, int32_t on);
+
 /* Diagnostic: poll budget of the in-kernel spin waits on global flags (the look-ahead tickets of
  * the blocked Cholesky factorisation and the block flags of the triangular solves).  polls >= 0:
  * such a wait gives up after that many polls, sets the timeout flag and the kernel continues

@@ -85,6 +85,7 @@ def _load():
         "icwf_get_stream": [H, P(ct.c_void_p)],
         "icwf_set_regularisation": [H, ct.c_double],
         "icwf_set_wait_limit": [H, ct.c_int64],
+        "icwf_set_step_graphs": [H, ct.c_int32],
         "icwf_profile_enable": [H, ct.c_int32],
         "icwf_profile_reset": [H],
         "icwf_profile_read": [H, ct.c_int32, P(ct.c_char_p), d, P(ct.c_int64), P(ct.c_int32)],
@@ -410,6 +411,9 @@ class Icwf:
 
     def set_wait_limit(self, polls):
         icwf_set_wait_limit(self.h, polls)
+
+    def set_step_graphs(self, on):
+        _check(LIB.icwf_set_step_graphs(self.h, 1 if on else 0), self.h)
 
     def release(self):
         """Give up ownership (after icwf_pool_submit the pool owns the handle)."""

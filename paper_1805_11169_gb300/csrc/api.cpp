@@ -116,6 +116,10 @@ struct icwf_ctx {
   int64_t launches = 0;   // kernels launched by icwf_step
   int prop_threads = 256; // CTA size of the CWF propagator (autotuned per shape at create)
   int64_t version = 0;    // bumped by calls that change captured kernel arguments (eps)
+  // icwf_step's captured step graphs (one per parity of the ping-pong buffers)
+  bool step_graphs = true;
+  cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+  int64_t step_exec_version = -1, step_kernels = 0;
   // profiling
   bool prof_on = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -431,6 +435,73 @@ void step_once(icwf_ctx* h) {
   h->cur = nxt;
   h->steps += 1;
   h->t += dt;
+}
+
+// Record two consecutive steps (not executed) into two graphs, g[p] for ping-pong parity p, and
+// restore the host-side step state; *kernels receives the kernels of one step.  Returns false
+// (with no graph left) if the capture fails.
+bool capture_step(icwf_ctx* h, cudaGraph_t g[2], int64_t* kernels) {
+  const bool prof = h->prof_on;
+  const int cur0 = h->cur;
+  const int64_t steps0 = h->steps, l0 = h->launches;
+  const double t0 = h->t;
+  h->prof_on = false;
+  g[0] = g[1] = nullptr;
+  bool ok = true;
+  for (int k = 0; k < 2 && ok; ++k) {
+    const int par = h->cur;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    step_once(h);
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamEndCapture(h->stream, &gr) != cudaSuccess || !gr) {
+      ok = false;
+      if (gr) cudaGraphDestroy(gr);
+      break;
+    }
+    g[par] = gr;
+  }
+  *kernels = (h->launches - l0) / 2;
+  h->cur = cur0;
+  h->steps = steps0;
+  h->t = t0;
+  h->launches = l0;
+  h->prof_on = prof;
+  if (!ok) {
+    for (int k = 0; k < 2; ++k)
+      if (g[k]) { cudaGraphDestroy(g[k]); g[k] = nullptr; }
+    cudaGetLastError();   // the failed capture's own error; the caller launches directly
+  }
+  return ok;
+}
+
+void drop_step_graphs(icwf_ctx* h) {
+  for (auto& e : h->step_exec)
+    if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+  h->step_exec_version = -1;
+}
+
+// The handle's instantiated step graphs, (re)built when missing or when a captured argument
+// changed; false if they cannot be built (icwf_step then launches directly).
+bool step_graphs_ready(icwf_ctx* h) {
+  if (h->step_exec[0] && h->step_exec_version == h->version) return true;
+  drop_step_graphs(h);
+  cudaGraph_t g[2];
+  if (!capture_step(h, g, &h->step_kernels)) return false;
+  bool ok = true;
+  for (int k = 0; k < 2; ++k) {
+    if (ok && cudaGraphInstantiate(&h->step_exec[k], g[k], 0) != cudaSuccess) ok = false;
+    cudaGraphDestroy(g[k]);
+  }
+  if (!ok) {
+    drop_step_graphs(h);
+    cudaGetLastError();
+    return false;
+  }
+  h->step_exec_version = h->version;
+  return true;
 }
 
 // ---- autotuner ------------------------------------------------------------------------------
@@ -778,6 +849,7 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
 icwf_status icwf_destroy(icwf_handle h) {
   if (!h) return ICWF_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_step_graphs(h);
   for (auto& pe : h->pending) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);
@@ -944,7 +1016,18 @@ icwf_status icwf_step(icwf_handle h, int32_t n_steps) {
   if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_step: NULL handle");
   if (!h->initialised) return fail(h, ICWF_ERR_STATE, "icwf_step: handle not initialised");
   if (n_steps < 0) return fail(h, ICWF_ERR_ARG, "icwf_step: n_steps < 0");
-  for (int s = 0; s < n_steps; ++s) step_once(h);
+  if (n_steps > 0 && h->step_graphs && !h->prof_on && step_graphs_ready(h)) {
+    // one graph launch per step (the per-family timing events need direct launches)
+    for (int s = 0; s < n_steps; ++s) {
+      CK(cudaGraphLaunch(h->step_exec[h->cur], h->stream));
+      h->cur = 1 - h->cur;
+      h->steps += 1;
+      h->t += h->p.dt;
+      h->launches += h->step_kernels;
+    }
+  } else {
+    for (int s = 0; s < n_steps; ++s) step_once(h);
+  }
   CK(cudaGetLastError());
   return sync_status(h, "icwf_step");
 }
@@ -1179,6 +1262,13 @@ icwf_status icwf_set_regularisation(icwf_handle h, double eps) {
   return ICWF_OK;
 }
 
+icwf_status icwf_set_step_graphs(icwf_handle h, int32_t on) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_set_step_graphs: NULL handle");
+  h->step_graphs = on != 0;
+  if (!h->step_graphs) drop_step_graphs(h);
+  return ICWF_OK;
+}
+
 icwf_status icwf_set_wait_limit(icwf_handle h, int64_t polls) {
   if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_set_wait_limit: NULL handle");
   if (polls > (int64_t)INT32_MAX - 1) return fail(h, ICWF_ERR_ARG, "icwf_set_wait_limit: polls too large");
@@ -1274,40 +1364,9 @@ void destroy_job_graphs(PoolJob& j) {
 // recorded, not executed), then restore the host-side step state.  Returns false (and leaves the
 // job to eager stepping) if the capture fails.
 bool capture_job_graphs(PoolJob& pj) {
-  icwf_ctx* h = pj.h;
-  const bool prof = h->prof_on;
-  const int cur0 = h->cur;
-  const int64_t steps0 = h->steps, l0 = h->launches;
-  const double t0 = h->t;
-  h->prof_on = false;
-  bool ok = true;
-  for (int k = 0; k < 2 && ok; ++k) {
-    const int par = h->cur;
-    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      ok = false;
-      break;
-    }
-    step_once(h);
-    cudaGraph_t g = nullptr;
-    if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess || !g) {
-      ok = false;
-      if (g) cudaGraphDestroy(g);
-      break;
-    }
-    pj.g[par] = g;
-  }
-  pj.kernels_per_step = (h->launches - l0) / 2;
-  h->cur = cur0;
-  h->steps = steps0;
-  h->t = t0;
-  h->launches = l0;
-  h->prof_on = prof;
-  if (!ok) {
-    destroy_job_graphs(pj);
-    cudaGetLastError();   // the failed capture's own error; the job steps eagerly instead
-  }
+  const bool ok = capture_step(pj.h, pj.g, &pj.kernels_per_step);
   pj.graphs_ok = ok;
-  pj.version = h->version;
+  pj.version = pj.h->version;
   return ok;
 }
 
