@@ -20,26 +20,27 @@
 // (integers), p + q = 3 (multiples of 1/B) and p + q >= 4 in three FP32 accumulators.  The first
 // two stay below 2^24 units (2 K B^2 <= 2^24: beta = 6 for K <= 2048, beta = 5 for K = 4096), so
 // their FP32 sums are exact; the third carries weight B^-2 relative to the first, so its FP32
-// rounding is below 1e-10 of S.  The epilogue adds the three in FP64 and scales by
-// dx 2^(e_a + e_b) B^-2.
+// rounding is of order 1e-10 of S or below.  The epilogue adds the three (double-float) and scales
+// by dx 2^(e_a + e_b) B^-2.
 //
 // Complex arithmetic on real MMAs: per digit pair, with P/Q the real/imaginary planes,
 //   [Re | Im] += P_a [P_b | Q_b] + Q_a [Q_b | -P_b],
 // one M = 128, N = 64 accumulator per level and side ([Re | Im] of 32 kets).
 //
 // Kernel layout (one CTA per 128 bras x 32 kets, upper triangle of 128 x 128 blocks, 192 threads):
-//   warp 4       TMA producer: per stage one 32-element K slice (64-byte rows, 64-byte swizzle)
+//   warp 4       TMA producer: per stage one 16-element K slice (32-byte rows, 32-byte swizzle)
 //                of the bra digit planes (4 digits x P, Q, 128 rows) and of the ket digit planes
-//                (4 digits x P, Q, -P, 32 rows each), two stages;
-//   warp 5       MMA issuer: 16 digit pairs x 2 planes x 2 K steps of 16 per stage;
-//   warps 0..3   epilogue: lane = bra a; S1, S2 in FP64 from TMEM, S = S1 o S2 for the block and
-//                its Hermitian mirror.
+//                (4 digits x P, Q, -P, 32 rows each), five stages;
+//   warp 5       MMA issuer: 16 digit pairs x 2 planes per stage (one K = 16 instruction each);
+//   warps 0..3   epilogue: lane = bra a; S1, S2 from TMEM in double-float arithmetic, S = S1 o S2
+//                for the block and its Hermitian mirror, stored in FP64.
 // Waits are bounded (2 s); a timeout raises the status flag, drains what is in flight and
 // returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
 #include "icwf_internal.h"
 #include "k_common.cuh"
 #include "tc_ptx.cuh"
@@ -52,14 +53,15 @@ using namespace tc;
 constexpr int BM = 128;                  // bras per CTA (TMEM lanes)
 constexpr int BNT = 32;                  // kets per CTA
 constexpr int DIG = 4;                   // digits per component
-constexpr int ROW = 64;                  // bytes per operand row per stage (32 BF16, 64-byte swizzle)
-constexpr int KEL = ROW / 2;             // K elements per stage
-constexpr int A_T = BM * ROW;            // one bra plane tile: 8 KB
+constexpr int ROW = 32;                  // bytes per operand row per stage (16 BF16, 32-byte swizzle)
+constexpr int KEL = ROW / 2;             // K elements per stage: one MMA instruction's K
+constexpr int A_T = BM * ROW;            // one bra plane tile: 4 KB
 constexpr int KETROWS = 3 * BNT;         // P, Q, -P of 32 kets
-constexpr int B_T = KETROWS * ROW;       // one ket digit block: 6 KB
-constexpr int STAGES = 2;
-constexpr int STAGE_BYTES = 2 * DIG * A_T + DIG * B_T;   // 64 KB + 24 KB
+constexpr int B_T = KETROWS * ROW;       // one ket digit block: 3 KB
+constexpr int STAGES = 5;                // four slices in flight hide the TMA latency
+constexpr int STAGE_BYTES = 2 * DIG * A_T + DIG * B_T;   // 32 KB + 12 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA exceeded");
 constexpr int TMEM_COLS = 512;
 constexpr int ACC_COLS = 2 * BNT;        // [Re | Im] of 32 kets
 constexpr int SIDE_COLS = 3 * ACC_COLS;  // three levels per side
@@ -174,14 +176,10 @@ __global__ void __launch_bounds__(192, 1) k_gram_s(Args args, const __grid_const
               const uint32_t acc = acc0 + lv * ACC_COLS;
               const uint32_t ap = st + (2 * p) * A_T, aq = ap + A_T;
               const uint32_t kq = kb + q * B_T;           // rows P | Q | -P of ket digit q
-#pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                const uint32_t o = kk * 32;                // 16 BF16 of K per instruction
-                const uint32_t first = started[lv] ? 1u : 0u;
-                mma_desc<0>(acc, sdesc_sw(ap + o, 64), sdesc_sw(kq + o, 64), IDESC, first);
-                mma_desc<0>(acc, sdesc_sw(aq + o, 64), sdesc_sw(kq + BNT * ROW + o, 64), IDESC, 1u);
-                started[lv] = true;
-              }
+              const uint32_t first = started[lv] ? 1u : 0u;
+              mma_desc<0>(acc, sdesc_sw(ap, ROW), sdesc_sw(kq, ROW), IDESC, first);
+              mma_desc<0>(acc, sdesc_sw(aq, ROW), sdesc_sw(kq + BNT * ROW, ROW), IDESC, 1u);
+              started[lv] = true;
             }
           }
           mma_commit(empty + slot);
@@ -208,10 +206,13 @@ __global__ void __launch_bounds__(192, 1) k_gram_s(Args args, const __grid_const
         : "memory");
     if (all_ok) {
       fence_after();
+      // the levels are combined and S1 o S2 formed in double-float arithmetic (FP32 pairs, ~2^-44
+      // relative; FP64 instructions are scarce on this GPU); FP64 only for the stores
       const int ea_x = a_ok ? args.ex[a] : 0, ea_R = a_ok ? args.eR[a] : 0;
+      const df dxd = df_from(args.dx), dRd = df_from(args.dR);
 #pragma unroll 1
       for (int c8 = 0; c8 < BNT; c8 += 8) {
-        double sr[2][8], si[2][8];
+        cdf sv[2][8];
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
           float v[3][2][8];
@@ -222,16 +223,18 @@ __global__ void __launch_bounds__(192, 1) k_gram_s(Args args, const __grid_const
           }
           tmem_wait_ld();
           const int beta = side ? args.beta_R : args.beta_x;
-          const double d = side ? args.dR : args.dx;
+          const df dd = side ? dRd : dxd;
           const int* eb = side ? args.eR : args.ex;
           const int ea = side ? ea_R : ea_x;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int b = b0 + c8 + e;
-            const int ebb = b < N ? eb[b] : 0;
-            const double sc = ldexp(d, ea + ebb - 2 * beta);
-            sr[side][e] = sc * (((double)v[0][0][e] + (double)v[1][0][e]) + (double)v[2][0][e]);
-            si[side][e] = sc * (((double)v[0][1][e] + (double)v[1][1][e]) + (double)v[2][1][e]);
+            const int sh = ea + (b < N ? eb[b] : 0) - 2 * beta;   // exact power-of-two scale
+            df re = df_add(two_sum(v[0][0][e], v[1][0][e]), df_make(v[2][0][e], 0.f));
+            df im = df_add(two_sum(v[0][1][e], v[1][1][e]), df_make(v[2][1][e], 0.f));
+            re = df_mul(df_make(ldexpf(re.h, sh), ldexpf(re.l, sh)), dd);
+            im = df_mul(df_make(ldexpf(im.h, sh), ldexpf(im.l, sh)), dd);
+            sv[side][e] = cdf_make(re, im);
           }
         }
 #pragma unroll
@@ -240,8 +243,9 @@ __global__ void __launch_bounds__(192, 1) k_gram_s(Args args, const __grid_const
           // each pair once, from its a <= b side (diagonal blocks compute both sides; the
           // highest-level sums of the two round differently), so S is exactly Hermitian
           if (b >= N || !a_ok || (!mirror && a > b)) continue;
-          const double r = sr[0][e] * sr[1][e] - si[0][e] * si[1][e];
-          const double i = a == b ? 0.0 : sr[0][e] * si[1][e] + si[0][e] * sr[1][e];
+          const cdf z = cdf_mul(sv[0][e], sv[1][e]);
+          const double r = df_to(z.re);
+          const double i = a == b ? 0.0 : df_to(z.im);
           args.S[(size_t)a * N + b] = make_double2(r, i);
           if (a != b) args.S[(size_t)b * N + a] = make_double2(r, -i);
         }
@@ -322,7 +326,7 @@ bool make_map64(CUtensorMap* m, void* base, int n, size_t rows, int box_rows) {
   cuuint32_t box[2] = {(cuuint32_t)KEL, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

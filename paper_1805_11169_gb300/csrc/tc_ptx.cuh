@@ -104,16 +104,16 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 
-// Shared-memory matrix descriptor of a K-major operand tile: swizzle 128 (rows of 128 bytes,
-// 8-row groups 1024 B apart) or 64 (rows of 64 bytes, 8-row groups 512 B apart).  The tile base
+// Shared-memory matrix descriptor of a K-major operand tile with rows of `swizzle` bytes (128,
+// 64 or 32) in the matching swizzle mode; 8-row groups are 8 * swizzle bytes apart.  The tile base
 // is aligned to its swizzle atom; a K offset inside the row is added to the start address.
 __device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr, int swizzle) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;                                   // leading-dimension offset (unused)
-  d |= (uint64_t)((swizzle == 128 ? 1024 : 512) >> 4) << 32;  // stride between 8-row groups
+  d |= (uint64_t)((8 * swizzle) >> 4) << 32;                // stride between 8-row groups
   d |= (uint64_t)1 << 46;                                   // descriptor version
-  d |= (uint64_t)(swizzle == 128 ? 2 : 4) << 61;            // swizzle mode
+  d |= (uint64_t)(swizzle == 128 ? 2 : (swizzle == 64 ? 4 : 6)) << 61;   // swizzle mode
   return d;
 }
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return sdesc_sw(saddr, 128); }
