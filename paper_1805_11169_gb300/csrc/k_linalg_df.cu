@@ -447,19 +447,47 @@ __device__ __forceinline__ void trtri_task(int N, const float4* A, const float2*
   }
 }
 
-__global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb, int nb, int li,
-                                                            unsigned* ctl, int* status) {
+// Control words of one factorisation call (zeroed before its first launch), per matrix m:
+//   ctl[li]                          ticket counter of launch li
+//   diag  [li][m]  at (T+2) + 2 li   finished quadrant updates of diagonal block li
+//   pdone [li][m]  at 3(T+2) + 2 li  diagonal factor of block li published
+//   slabdone[m][l][b]                finished 8-row panel slabs of launch l in row block b
+//   tilecnt [m][r][c]                trailing updates applied to tile (r, c)
+// Tasks wait (bounded) on these rather than on the end of the previous launch, so the chain of
+// block column li + 1 (quadrants -> diagonal factor -> panel) overlaps the trailing updates of
+// launch li.
+struct CholCtl {
+  unsigned *slabdone, *tilecnt;
+  int T, N;
+  __device__ unsigned* sd(int m, int l, int b) const { return slabdone + ((size_t)m * (T + 1) + l) * T + b; }
+  __device__ unsigned* tc(int m, int r, int c) const { return tilecnt + ((size_t)m * T + r) * T + c; }
+  __device__ unsigned slabs_in(int b) const {
+    const int rows = N - b * NB < NB ? N - b * NB : NB;
+    return (unsigned)((rows + TS_ROWS - 1) / TS_ROWS);
+  }
+};
+
+// thread 0 waits (bounded) until *f >= target, then fences; the caller synchronises the CTA
+__device__ __forceinline__ void wait_count(const unsigned* f, unsigned target, int* status) {
+  if (threadIdx.x == 0 && target > 0) {
+    cs_wait(f, target, status);
+    __threadfence();
+  }
+}
+
+__device__ __forceinline__ void chol_task(int N, Batch mb, int nb, int li, unsigned* ctl,
+                                          int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ unsigned s_t;
   const int T = (N + NB - 1) / NB;
   const int jp = li, jb = li - 1;
   unsigned* diag = ctl + (T + 2) + 2 * li;     // [li][matrix]: finished quadrants
   unsigned* pdone = ctl + 3 * (T + 2) + 2 * li;  // [li][matrix]: diagonal factor published
-  // programmatic dependent launch: the next block column's launch may become resident now; this
-  // launch reads nothing of the previous one's output before griddepcontrol.wait, which returns
-  // once the previous launch has completed and its writes are visible
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  CholCtl cc;
+  cc.slabdone = ctl + 5 * (T + 2);
+  cc.tilecnt = cc.slabdone + 2 * (size_t)(T + 1) * T;
+  cc.T = T;
+  cc.N = N;
   if (threadIdx.x == 0) s_t = atomicAdd(ctl + li, 1u);
   __syncthreads();
   int t = (int)s_t;
@@ -469,9 +497,13 @@ __global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb,
   const int rows = N - (jp + 1) * NB;
   const int nslab = (jp < T && rows > 0) ? (rows + TS_ROWS - 1) / TS_ROWS : 0;
   if (t < nb * ndiag) {
-    // quadrant (rh, ch) of diagonal block jp: A -= L_jp,jb L_jp,jb^H
+    // quadrant (rh, ch) of diagonal block jp: A -= L_jp,jb L_jp,jb^H; needs panel jb on the rows
+    // of block jp and the jb earlier trailing updates of the diagonal tile
     const int m = t % nb, qd = t / nb;
     const int rh = qd > 0 ? 1 : 0, ch = qd > 1 ? 1 : 0;
+    wait_count(cc.sd(m, jb, jp), cc.slabs_in(jp), status);
+    wait_count(cc.tc(m, jp, jp), (unsigned)jb, status);
+    __syncthreads();
     float4* A = pick2(mb.m, m);
     const int r = threadIdx.x / 16, c = threadIdx.x % 16;
     const int orow = jp * NB + rh * 16 + r, ocol = jp * NB + ch * 16 + c;
@@ -500,8 +532,10 @@ __global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb,
   t -= nb * npotrf;
   const int ntrtri = jp >= 1 ? 1 : 0;
   if (t < nb * ntrtri) {
-    // inverse of the previous diagonal block (final since the previous launch), for the solves
+    // inverse of the previous diagonal block (final once its factor is published), for the solves
     const int m = t;
+    wait_count(ctl + 3 * (T + 2) + 2 * (li - 1) + m, 1u, status);
+    __syncthreads();
     trtri_task(N, pick2(mb.m, m), pick2(mb.inv, m), pick2(mb.D, m), jp - 1, sm);
     return;
   }
@@ -510,7 +544,14 @@ __global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb,
     const int m = t % nb;
     int I, J;
     tri_index(t / nb, I, J);
-    herk_tile(pick2(mb.m, m), N, jb, jb + 2 + J, jb + 2 + I, sm);
+    const int rb = jb + 2 + J, cb = jb + 2 + I;
+    // panel jb on both row blocks, and the tile's jb - 1 earlier updates
+    wait_count(cc.sd(m, jb, rb), cc.slabs_in(rb), status);
+    wait_count(cc.sd(m, jb, cb), cc.slabs_in(cb), status);
+    wait_count(cc.tc(m, rb, cb), (unsigned)(jb > 0 ? jb : 0), status);
+    __syncthreads();
+    herk_tile(pick2(mb.m, m), N, jb, rb, cb, sm);
+    cs_signal(cc.tc(m, rb, cb));
     return;
   }
   t -= nb * nherk;
@@ -523,6 +564,14 @@ __global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb,
     const int i0 = (jp + 1) * NB + sl * TS_ROWS;
     const int r = threadIdx.x / NB, c = threadIdx.x % NB;
     const bool ok = i0 + r < N;
+    const int bi = i0 / NB;
+    if (jb >= 0) {
+      // panel jb on these rows and on the rows of block jp, and the tile's jb earlier updates
+      wait_count(cc.sd(m, jb, bi), cc.slabs_in(bi), status);
+      wait_count(cc.sd(m, jb, jp), cc.slabs_in(jp), status);
+      wait_count(cc.tc(m, bi, jp), (unsigned)jb, status);
+      __syncthreads();
+    }
     cdf a;
     if (jb >= 0) a = upd_one<TS_ROWS, NB>(A, N, i0, jp * NB, jb * NB, i0 + r, jp * NB + c, ok, sm);
     else a = ok ? ldcg4(A + (size_t)(i0 + r) * N + jp * NB + c) : czero();
@@ -563,7 +612,19 @@ __global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb,
       // L^H in the (otherwise unused) upper triangle: the backward solve reads it by rows
       A[(size_t)(jp * NB + c) * N + i0 + r] = st4(cdf_make(x.re, df_neg(x.im)));
     }
+    cs_signal(cc.sd(m, li, bi));
   }
+}
+
+__global__ void __launch_bounds__(CS_THREADS, 3) k_chol_step_df(int N, Batch mb, int nb, int li,
+                                                            unsigned* ctl, int* status) {
+  // programmatic dependent launch: the next block column's launch may become resident at once;
+  // its tasks wait on the control words for exactly the data they read
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  chol_task(N, mb, nb, li, ctl, status);
+  // the grid completes only after its predecessor has, so later work in the stream sees the whole
+  // factorisation
+  if (threadIdx.x == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------- triangular solves
@@ -1135,7 +1196,10 @@ int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, 
   return T + 2;
 }
 
-size_t chol_ctl_words(int N) { return (size_t)5 * ((N + dfs::NB - 1) / dfs::NB + 2); }
+size_t chol_ctl_words(int N) {
+  const size_t T = (N + dfs::NB - 1) / dfs::NB;
+  return 5 * (T + 2) + 2 * (T + 1) * T + 2 * T * T;
+}
 
 void launch_chol_solve_df(int N, const void* L, const void* D, const double2* y, void* work,
                           double2* out, bool minus_i, unsigned* flags, unsigned* tickets,
