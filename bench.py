@@ -444,6 +444,8 @@ def run_ours(args, rank, ws, local):
         out["rank_error"] = run_rank_error(args.mode)
         if args.mode != "fp64":
             out["mixed_vs_fp64"] = run_mixed_vs_fp64(args.mode, eps)
+            if args.solve != "fp64":
+                out["solve_fp64"] = run_solve_fp64(args.mode, eps, local)
         out["cavity"] = run_cavity_line(args, local, peaks)
     if rank == 0 and not args.no_exact2d:
         out["exact2d"] = run_exact2d(w)
@@ -569,14 +571,28 @@ def run_vs_exact(w, prec, steps, every, seed, overlap_split=0):
             "max_pop_err": max(r["pop_max_err"] for r in rows), "wall_s": wall}
 
 
+def init_residual(sim, w):
+    """||(S + eps I) C - b|| / ||b|| of an FP64-mode handle right after initialisation, with
+    b_a = <psi_a chi_a | Psi0> formed here from the handle's own FP64 CWFs (the slices the
+    library projected) and S as stored."""
+    import numpy as np
+    st = sim.state()
+    S = sim.matrices()["S"]
+    b = w.dx * w.dR * np.sum(st["psi"].conj() * (w.psi0 @ st["chi"].conj()), axis=0)
+    r = (S + w.s_reg_eps * np.eye(w.n_traj)) @ st["C"] - b
+    return float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
 def run_fp64_comparison(steps=10, warmup=2):
-    """The same workload in FP64 mode (same GB300, same process): trajectory-steps/s."""
+    """The same workload in FP64 mode (same GB300, same process): trajectory-steps/s, and the
+    residual of the initial solve (FP64 solver, emulated-FP64 trailing updates)."""
     import torch
     import paper_1805_11169_gb300 as g
     prec, dtype_name, cutoff, eps = MODES["fp64"]
     w = make_workload(1024, cutoff, eps)
     sim = g.Icwf(g.params_from(w, precision=prec), w.V)
     sim.init_from_density(w.psi0, w.seed)
+    resid = init_residual(sim, w)
     stream = torch.cuda.ExternalStream(sim.stream())
     for _ in range(warmup):
         sim.step(1)
@@ -592,7 +608,36 @@ def run_fp64_comparison(steps=10, warmup=2):
     sim.close()
     return {"value": w.n_traj * steps / (ms / 1e3), "unit": "trajectory-steps/s",
             "ms_per_step": ms / steps, "dtype": dtype_name, "rank_k": k, "steps": steps,
-            "svd_rel_cutoff": cutoff, "s_reg_eps": eps}
+            "svd_rel_cutoff": cutoff, "s_reg_eps": eps, "init_solve_residual": resid}
+
+
+def run_solve_fp64(mode, eps, local, steps=30, warmup=3):
+    """The headline configuration with the FP64 solver (solve_fp64 = 1): trajectory-steps/s and the
+    factorisation's time per call, with its trailing updates in emulated FP64 on the tensor cores
+    (the default) and with FP64 FMAs; plus the initial-solve residual of the same solver in FP64
+    mode on this workload."""
+    import paper_1805_11169_gb300 as g
+    prec, _, cutoff, _ = MODES[mode]
+    w = make_workload(1024, cutoff, eps)
+    out = {"s_reg_eps": eps}
+    for name, emu, n in (("emulated_update", 1, steps), ("fma_update", 0, max(5, steps // 3))):
+        sim = g.Icwf(g.params_from(w, precision=prec, solve_fp64=1), w.V)
+        sim.set_emulated_update(emu)
+        sim.set_projectors(w.phi)
+        sim.init_from_density(w.psi0, w.seed)
+        total_ms, prof, _, clocks, _ = timed_steps(sim, n, warmup, local, prof_steps=10)
+        sim.close()
+        ch = prof.get("cholesky", (0.0, 0))
+        out[name] = {"value": w.n_traj * n / (total_ms / 1e3), "ms_per_step": total_ms / n,
+                     "steps": n, "cholesky_ms_per_call": ch[0] / max(ch[1], 1) if ch[1] else None,
+                     "clocks": clocks}
+    sim = g.Icwf(g.params_from(w, precision=MODES["fp64"][0]), w.V)
+    sim.init_from_density(w.psi0, w.seed)
+    out["init_solve_residual_fp64_mode"] = init_residual(sim, w)
+    sim.close()
+    out["value"] = out["emulated_update"]["value"]
+    out["unit"] = "trajectory-steps/s"
+    return out
 
 
 def run_rank_error(mode, steps=10, n_cols=16):

@@ -52,7 +52,8 @@ typedef enum {
 
 typedef enum {
   ICWF_FP64 = 0,          /* CWFs complex128; matrix elements, Cholesky, triangular solves and
-                             RK4 in FP64 */
+                             RK4 in FP64 (the factorisation's trailing updates in emulated FP64
+                             on the tensor cores unless icwf_set_emulated_update turns it off) */
   ICWF_MIXED_BF16X3 = 1,  /* CWFs complex64, FP32 propagation; Grams on tcgen05 tensor cores as
                              three BF16 products (hi*hi + hi*lo + lo*hi), FP32 accumulation;
                              the overlap S as an exact Gram of fixed-point CWFs (positive
@@ -207,6 +208,18 @@ icwf_status icwf_heff_direct(icwf_handle h, int32_t n_cols, const int32_t* cols,
  * value is accepted; a negative eps makes S + eps I indefinite, so the next step's Cholesky
  * fails and returns ICWF_ERR_NUMERIC (the failure path the tests drive on purpose). */
 icwf_status icwf_set_regularisation(icwf_handle h, double eps);
+
+/* FP64 solver (ICWF_FP64, or solve_fp64 in the mixed modes): how the blocked Cholesky
+ * factorisation forms its trailing updates A_rc -= L_r L_c^H (a Hermitian rank-32 update per block
+ * column; the bulk of the factorisation's arithmetic).  on = 1 (default): on the tensor cores in
+ * emulated FP64 -- each row of the 32-wide panel is scaled by a power of two and cut into seven
+ * 8-bit digits held exactly in BF16; the digit products up to the eighth level are summed exactly
+ * in FP32 accumulators (the leading four levels each in their own) and combined in double-float,
+ * so every update element carries an error of about 2^-47 of |L_r| |L_c| (an FP64 dot product of
+ * 32 terms: up to about 2^-48).  on = 0: FP64 fused multiply-adds.  The diagonal-block factors,
+ * the panel solves and the triangular solves stay in FP64 either way.  Ignored by handles whose
+ * solver is double-float.  The step graphs are re-recorded on the next step. */
+icwf_status icwf_set_emulated_update(icwf_handle h, int32_t on);
 
 /* icwf_step replays each time step as a captured CUDA graph (recorded on the first call, one
  * graph per parity of the ping-pong matrix buffers; re-recorded after icwf_set_regularisation)

@@ -86,6 +86,7 @@ def _load():
         "icwf_set_regularisation": [H, ct.c_double],
         "icwf_set_wait_limit": [H, ct.c_int64],
         "icwf_set_step_graphs": [H, ct.c_int32],
+        "icwf_set_emulated_update": [H, ct.c_int32],
         "icwf_profile_enable": [H, ct.c_int32],
         "icwf_profile_reset": [H],
         "icwf_profile_read": [H, ct.c_int32, P(ct.c_char_p), d, P(ct.c_int64), P(ct.c_int32)],
@@ -414,6 +415,11 @@ class Icwf:
 
     def set_step_graphs(self, on):
         _check(LIB.icwf_set_step_graphs(self.h, 1 if on else 0), self.h)
+
+    def set_emulated_update(self, on):
+        """FP64 solver: trailing updates of the factorisation on the tensor cores in emulated FP64
+        (default) or with FP64 FMAs."""
+        _check(LIB.icwf_set_emulated_update(self.h, 1 if on else 0), self.h)
 
     def release(self):
         """Give up ownership (after icwf_pool_submit the pool owns the handle)."""

@@ -109,6 +109,10 @@ struct icwf_ctx {
   // tensor-core assembly scratch
   void* tc_scratch = nullptr;
   size_t tc_scratch_bytes = 0;
+  // FP64 factorisation: digit planes of the emulated trailing update (allocated when !df_solve)
+  void* emu_scratch = nullptr;
+  size_t emu_bytes = 0;
+  bool emu_update = true;                   // trailing updates on the tensor cores
   // state
   bool initialised = false;
   int64_t steps = 0;
@@ -323,7 +327,8 @@ void factor(icwf_ctx* h, int n, const double2* const* S0, const double2* const* 
     void* dd[2] = {D[0], n > 1 ? D[1] : D[0]};
     h->launches += launch_cholesky_df(h->N, a, iv, dd, n, h->cctl, h->status, h->stream);
   } else {
-    h->launches += launch_cholesky(h->N, dst, inv, D, n, h->status, h->stream);
+    h->launches += launch_cholesky(h->N, dst, inv, D, n, h->status, h->stream,
+                                   h->emu_update ? h->emu_scratch : nullptr, h->emu_bytes);
   }
 }
 
@@ -745,6 +750,11 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
     h->tc_scratch_bytes = assemble_tc_scratch_bytes(N, nx, nR, K);
     total += align256(h->tc_scratch_bytes);
   }
+  if (!h->df_solve) {
+    h->emu_bytes = herk_emu_scratch_bytes(N);
+    total += align256(h->emu_bytes);
+    herk_emu_attributes();
+  }
   total += 4096;
   if (cudaMalloc(&h->arena.base, total) != cudaSuccess) {
     destroy_streams(h);
@@ -796,7 +806,8 @@ icwf_status icwf_create(const icwf_params* pp, const double* Vh, icwf_handle* ou
   h->cctl = (unsigned*)a.take(chol_ctl_words(N) * sizeof(unsigned));
   h->status = (int*)a.take(64 * 4);
   if (h->mixed) h->tc_scratch = a.take(h->tc_scratch_bytes);
-  if (!h->status || (h->mixed && !h->tc_scratch)) {
+  if (!h->df_solve) h->emu_scratch = a.take(h->emu_bytes);
+  if (!h->status || (h->mixed && !h->tc_scratch) || (!h->df_solve && !h->emu_scratch)) {
     cudaFree(h->arena.base);
     destroy_streams(h);
     return fail(nullptr, ICWF_ERR_OOM, "icwf_create: arena layout overflow");
@@ -1259,6 +1270,13 @@ icwf_status icwf_set_regularisation(icwf_handle h, double eps) {
   if (!std::isfinite(eps)) return fail(h, ICWF_ERR_ARG, "icwf_set_regularisation: eps is not finite");
   h->p.s_reg_eps = eps;
   h->version += 1;   // a pool re-captures this job's step graphs
+  return ICWF_OK;
+}
+
+icwf_status icwf_set_emulated_update(icwf_handle h, int32_t on) {
+  if (!h) return fail(nullptr, ICWF_ERR_ARG, "icwf_set_emulated_update: NULL handle");
+  h->emu_update = on != 0;
+  h->version += 1;   // the step graphs hold the previous update kernels: re-capture them
   return ICWF_OK;
 }
 

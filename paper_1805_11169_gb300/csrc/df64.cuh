@@ -72,6 +72,12 @@ DF_HD df df_add(df a, df b) {
   s.l = DF_ADD(s.l, t.l);
   return fast_two_sum(s.h, s.l);
 }
+// a + b for an FP32 b: TwoSum of the high parts, one renormalisation (error ~2^-48 of |a + b|
+// when |a.l| <= ulp(a.h) / 2)
+DF_HD df df_add_f(df a, float b) {
+  const df s = two_sum(a.h, b);
+  return fast_two_sum(s.h, DF_ADD(s.l, a.l));
+}
 DF_HD df df_neg(df a) { return df_make(-a.h, -a.l); }
 DF_HD df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 

@@ -93,9 +93,18 @@ void launch_shift_mix(int N, const double2* S0, const double2* S1, double eps, d
                       double2* A, cudaStream_t s);
 // Right-looking blocked Cholesky of nbatch <= 2 matrices in place (lower triangle = L); inv[m]
 // receives the N reciprocal pivots 1/L_cc and D[m] (N x 32 complex) the inverses of the 32 x 32
-// diagonal blocks.  Returns the number of kernels launched.
+// diagonal blocks.  With emu_scratch (herk_emu_scratch_bytes(N) bytes) the trailing updates run
+// on the tensor cores in emulated FP64 (k_herk_emu.cu), else with FP64 FMAs.  Returns the number
+// of kernels launched.
 int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const* D, int nbatch,
-                    int* status, cudaStream_t s);
+                    int* status, cudaStream_t s, void* emu_scratch = nullptr, size_t emu_bytes = 0);
+// Trailing update A_rc -= L_r,jb L_c,jb^H (c <= r, both past block column jb) of nbatch <= 2
+// matrices in emulated FP64 on the tensor cores: two launches (digit planes, update).  False if
+// the scratch is too small or a tensor map cannot be encoded (nothing launched then).
+size_t herk_emu_scratch_bytes(int N);
+bool launch_herk_emu(int N, int jb, double2* const* A, int nbatch, void* scratch, size_t bytes,
+                     int* status, cudaStream_t s);
+void herk_emu_attributes();
 // y = ((1-theta) H0 + theta H1) (C + c * kp)      (kp may be NULL)
 void launch_matvec(int N, const double2* H0, const double2* H1, double theta, const double2* C,
                    const double2* kp, double c, double2* y, cudaStream_t s);

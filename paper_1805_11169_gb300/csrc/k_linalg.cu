@@ -1,9 +1,11 @@
 // FP64 linear algebra of the coefficient update (Eq. coeff, S dC/dt = -i Heff C): the
 // Tikhonov-shifted overlap S + eps I, its blocked Cholesky factorisation, the two triangular
 // solves, the Heff matrix-vector products of the RK4 stages and the final RK4 combination.
-// All arithmetic here is FP64 (S is near-singular as CWFs overlap).  The FP64 mode and the
-// solve_fp64 option of the mixed modes factorise and solve with these kernels; the mixed modes'
-// default solver is the double-float one of k_linalg_df.cu.
+// All arithmetic here is FP64 (S is near-singular as CWFs overlap); the factorisation's trailing
+// updates run either here with FP64 FMAs or in emulated FP64 on the tensor cores (exact integer
+// digit products, k_herk_emu.cu).  The FP64 mode and the solve_fp64 option of the mixed modes
+// factorise and solve with these kernels; the mixed modes' default solver is the double-float one
+// of k_linalg_df.cu.
 #include <cuda_runtime.h>
 
 #include "icwf_internal.h"
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(256) k_herk_update(int N, MatBatch mb, int jb)
 }
 
 int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const* D, int nbatch,
-                    int* status, cudaStream_t s) {
+                    int* status, cudaStream_t s, void* emu_scratch, size_t emu_bytes) {
   MatBatch mb;
   mb.m[0] = A[0];
   mb.m[1] = nbatch > 1 ? A[1] : A[0];
@@ -269,8 +271,12 @@ int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const
     if (rest > 0) {
       const int rows = N - (jb + 1) * NB;
       k_trsm_panel<<<dim3((rows + TR_WARPS - 1) / TR_WARPS, nbatch), TR_WARPS * 32, 0, s>>>(N, mb, jb);
-      k_herk_update<<<dim3(rest * (rest + 1) / 2, nbatch), 256, 0, s>>>(N, mb, jb);
-      launches += 2;
+      if (emu_scratch && launch_herk_emu(N, jb, A, nbatch, emu_scratch, emu_bytes, status, s)) {
+        launches += 3;
+      } else {
+        k_herk_update<<<dim3(rest * (rest + 1) / 2, nbatch), 256, 0, s>>>(N, mb, jb);
+        launches += 2;
+      }
     }
   }
   k_trtri_diag<<<dim3(T, nbatch), 128, 0, s>>>(N, mb);
