@@ -99,11 +99,14 @@ void launch_shift_mix(int N, const double2* S0, const double2* S1, double eps, d
 int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const* D, int nbatch,
                     int* status, cudaStream_t s, void* emu_scratch = nullptr, size_t emu_bytes = 0);
 // Trailing update A_rc -= L_r,jb L_c,jb^H (c <= r, both past block column jb) of nbatch <= 2
-// matrices in emulated FP64 on the tensor cores: two launches (digit planes, update).  False if
-// the scratch is too small or a tensor map cannot be encoded (nothing launched then).
+// matrices in emulated FP64 on the tensor cores: the panel's digit planes (unless digits_done:
+// the panel solve wrote them) and the update.  False if the scratch is too small or a tensor map
+// cannot be encoded (nothing launched then).
 size_t herk_emu_scratch_bytes(int N);
+struct EmuPlanes { void* planes[2]; int* ex[2]; int rpad; };   // digit planes inside the scratch
+EmuPlanes herk_emu_planes(int N, void* scratch);
 bool launch_herk_emu(int N, int jb, double2* const* A, int nbatch, void* scratch, size_t bytes,
-                     int* status, cudaStream_t s);
+                     bool digits_done, int* status, cudaStream_t s);
 void herk_emu_attributes();
 // y = ((1-theta) H0 + theta H1) (C + c * kp)      (kp may be NULL)
 void launch_matvec(int N, const double2* H0, const double2* H1, double theta, const double2* C,

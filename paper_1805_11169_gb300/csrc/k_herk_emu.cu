@@ -25,17 +25,20 @@
 // pair takes four MMAs (K = 16 each), 28 pairs in all.
 //
 // Kernel layout: one CTA per (128-row tile, 32-column tile) of the trailing matrix that meets its
-// lower triangle, 192 threads; warp 4 loads the whole K = 32 slice of all digit planes with TMA
-// (64-byte rows and swizzle, one stage, 168 KB), warp 5 issues the 112 MMAs, warps 0..3 run the
-// epilogue.  Waits are bounded (2 s): a timeout raises the status flag, drains what is in flight
+// lower triangle, 576 threads; warp 16 loads the whole K = 32 slice of all digit planes with TMA
+// (64-byte rows and swizzle, one stage, 168 KB), warp 17 issues the 112 MMAs, warps 0..15 run the
+// epilogue (warp w reads TMEM lanes 32 (w mod 4).. and columns 8 (w div 4)..: four warps per SM
+// sub-partition hide each other's dependent chains).  Waits are bounded (2 s): a timeout raises the status flag, drains what is in flight
 // and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "df64.cuh"
+#include "herk_digits.cuh"
 #include "icwf_internal.h"
 #include "k_common.cuh"
 #include "tc_ptx.cuh"
@@ -45,11 +48,7 @@ namespace hemu {
 
 using namespace tc;
 
-constexpr int NB = 32;                 // block size of the factorisation (panel width = K)
-constexpr int DIG = 7;                 // digits per component
-constexpr int BETA = 8;                // digit base 2^8
 constexpr int NLEV = 7;                // kept levels p + q = 0..6 (0-based digits)
-constexpr int PLANES = 4;              // P, -Q, Q, P
 constexpr int BM = 128;                // rows per CTA (TMEM lanes)
 constexpr int BNC = 32;                // columns per CTA
 constexpr int ROW = 64;                // bytes per operand row (32 BF16)
@@ -63,6 +62,10 @@ constexpr int ACC = 2 * BNC;           // [Re | Im]
 static_assert(NLEV * ACC <= TMEM_COLS, "accumulators exceed the TMEM allocation");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA exceeded");
 constexpr uint32_t IDESC = idesc_mn(0, BM, ACC);
+constexpr int EPI_WARPS = 16;          // epilogue warps: 4 TMEM lane quarters x 4 column quarters
+constexpr int TMA_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
+constexpr int EMU_THREADS = (EPI_WARPS + 2) * 32;
+constexpr int EPI_COLS = BNC / (EPI_WARPS / 4);   // columns per epilogue warp
 
 struct Maps {
   CUtensorMap a[2], b[2];   // per matrix: 128-row boxes (rows r), 32-row boxes (columns c)
@@ -75,27 +78,8 @@ struct Args {
   int* status;
 };
 
-// round(|x| 2^(63 - e)) for |x| < 2^e, from the FP64 bit pattern with integer operations only.
-__device__ __forceinline__ unsigned long long fixed63(unsigned long long u, int e) {
-  const int E = (int)((u >> 52) & 0x7FFu);
-  const unsigned long long frac = u & 0xFFFFFFFFFFFFFull;
-  const unsigned long long mant = E ? (frac | (1ull << 52)) : frac;   // |x| = mant 2^p2
-  const int p2 = E ? E - 1075 : -1074;
-  const int s = p2 + 63 - e;              // <= 10 since |x| < 2^e
-  if (s >= 0) return mant << s;
-  if (s <= -54) return 0;                 // below half a unit
-  return (mant + (1ull << (-s - 1))) >> (-s);
-}
-
-// Exponent e with max|x| < 2^e (e = 0 for an all-zero row) from the largest |x|'s bit pattern.
-__device__ __forceinline__ int row_exponent(unsigned long long mbits) {
-  const int E = (int)(mbits >> 52);
-  if (E) return E - 1022;
-  return mbits ? -1074 + (64 - __clzll((long long)mbits)) : 0;
-}
-
-// Digit planes of the panel rows i in [R0, N) of one matrix (one warp per row, lane = column k):
-// planes[((p * 4 + pi) * rpad + i) * 32 + k].  Integer and FP32 instructions only.
+// Digit planes of the panel rows i in [R0, N) of one matrix (one warp per row, lane = column k),
+// for panels that were not produced by the FP64 panel solve.
 __global__ void __launch_bounds__(256) k_panel_digits(const double2* __restrict__ A0,
                                                       const double2* __restrict__ A1, int N, int jb,
                                                       int rpad, __nv_bfloat16* __restrict__ pl0,
@@ -103,45 +87,10 @@ __global__ void __launch_bounds__(256) k_panel_digits(const double2* __restrict_
                                                       int* __restrict__ ex0, int* __restrict__ ex1) {
   const int m = blockIdx.y;
   const double2* A = m ? A1 : A0;
-  __nv_bfloat16* planes = m ? pl1 : pl0;
-  int* ex = m ? ex1 : ex0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = (jb + 1) * NB + blockIdx.x * 8 + warp;
   if (i >= N) return;
-  const double2 z = A[(size_t)i * N + jb * NB + lane];
-  const unsigned long long ur = (unsigned long long)__double_as_longlong(z.x);
-  const unsigned long long ui = (unsigned long long)__double_as_longlong(z.y);
-  const unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
-  // magnitudes of non-negative doubles order like their bit patterns
-  unsigned long long mb = (ur & ABS) > (ui & ABS) ? (ur & ABS) : (ui & ABS);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mb, off);
-    mb = o > mb ? o : mb;
-  }
-  const int e = row_exponent(mb);
-  if (lane == 0) ex[i] = e;
-  // signed fixed-point values X = round(x 2^(63 - e)), |X| <= 2^63 - 2^10
-  long long xr = (long long)fixed63(ur & ABS, e), xi = (long long)fixed63(ui & ABS, e);
-  if (ur >> 63) xr = -xr;
-  if (ui >> 63) xi = -xi;
-  const size_t pl = (size_t)rpad * NB;
-#pragma unroll
-  for (int p = 0; p < DIG; ++p) {
-    const int sh = 55 - BETA * p;         // digit p weighs 2^sh units of 2^(e - 63)
-    // balanced digit: round half up of X / 2^sh, then X -= d 2^sh (two's complement wrap-free:
-    // the remainder is at most 2^(sh - 1))
-    const long long dr = ((xr >> (sh - 1)) + 1) >> 1, di = ((xi >> (sh - 1)) + 1) >> 1;
-    xr = (long long)((unsigned long long)xr - ((unsigned long long)dr << sh));
-    xi = (long long)((unsigned long long)xi - ((unsigned long long)di << sh));
-    const float w = __int_as_float((127 - BETA * p) << 23);   // 2^(-8 p), exact
-    const float fr = (float)dr * w, fi = (float)di * w;
-    const size_t base = (size_t)(p * PLANES) * pl + (size_t)i * NB + lane;
-    planes[base] = __float2bfloat16_rn(fr);            // P
-    planes[base + pl] = __float2bfloat16_rn(-fi);      // -Q
-    planes[base + 2 * pl] = __float2bfloat16_rn(fi);   // Q
-    planes[base + 3 * pl] = __float2bfloat16_rn(fr);   // P
-  }
+  emit_row_digits(A[(size_t)i * N + jb * NB + lane], i, lane, rpad, m ? pl1 : pl0, m ? ex1 : ex0);
 }
 
 // x 2^sh as FP64 from an FP32 x by integer arithmetic on the exponent field (FP64 instructions are
@@ -162,11 +111,19 @@ __device__ __forceinline__ double f32_scaled(float x, int sh) {
 }
 
 
-__global__ void __launch_bounds__(192, 1) k_herk_emu(Args args, const __grid_constant__ Maps maps) {
+__global__ void __launch_bounds__(EMU_THREADS, 1) k_herk_emu(Args args, const __grid_constant__ Maps maps) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const int I = blockIdx.x, J = blockIdx.y, m = blockIdx.z;
-  // only tiles that meet the lower triangle (some column <= some row)
-  if (J * BNC > I * BM + BM - 1) return;
+  // linear index over the tiles that meet the lower triangle (some column <= some row): row tile
+  // I holds min(4 (I + 1), nJ) column tiles
+  const int m = blockIdx.y;
+  int I = 0, J = (int)blockIdx.x;
+  while (I < args.nI) {
+    const int cnt = min((BM / BNC) * (I + 1), args.nJ);
+    if (J < cnt) break;
+    J -= cnt;
+    ++I;
+  }
+  if (I >= args.nI) return;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + SM_A + SM_B);
   uint64_t* acc_full = full + 1;
@@ -193,7 +150,7 @@ __global__ void __launch_bounds__(192, 1) k_herk_emu(Args args, const __grid_con
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  if (warp == 4) {
+  if (warp == TMA_WARP) {
     if (lane == 0) {
       mbar_expect_tx(full, SM_A + SM_B);
       for (int p = 0; p < DIG; ++p) {
@@ -204,27 +161,26 @@ __global__ void __launch_bounds__(192, 1) k_herk_emu(Args args, const __grid_con
                       (p * PLANES + pi) * rpad + c0, full);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == MMA_WARP) {
     if (lane == 0) {
       if (mbar_wait(full, 0u, abort_flag, args.status)) {
         fence_after();
-        const uint32_t sa = smem_u32(smem), sb = smem_u32(smem + SM_A);
-        uint32_t started = 0;   // bit lv: accumulator lv holds a partial sum
-#pragma unroll 1
+        // descriptors of the operand tiles as base + (byte offset >> 4): the start-address field
+        // holds address / 16 in its low 14 bits and shared addresses stay below 256 KB
+        const uint64_t da = sdesc_sw(smem_u32(smem), 64), db = sdesc_sw(smem_u32(smem + SM_A), 64);
+#pragma unroll
         for (int p = 0; p < DIG; ++p) {
-#pragma unroll 1
+#pragma unroll
           for (int q = 0; p + q < NLEV && q < DIG; ++q) {
-            const int lv = p + q;
-            const uint32_t acc = tmem + lv * ACC;
-            const uint32_t ap = sa + (2 * p) * A_T, aq = ap + A_T;
-            const uint32_t bq = sb + q * B_T;   // rows P | -Q | Q | P of digit q
+            const uint32_t acc = tmem + (p + q) * ACC;
+            const uint64_t ap = da + ((2 * p) * A_T >> 4), aq = ap + (A_T >> 4);
+            const uint64_t bq = db + (q * B_T >> 4);     // rows P | -Q | Q | P of digit q
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-              const uint32_t o = kk * 32;       // 16 BF16 of K per instruction
-              mma_desc<0>(acc, sdesc_sw(ap + o, 64), sdesc_sw(bq + o, 64), IDESC,
-                          (started >> lv) & 1u);
-              mma_desc<0>(acc, sdesc_sw(aq + o, 64), sdesc_sw(bq + 2 * BNC * ROW + o, 64), IDESC, 1u);
-              started |= 1u << lv;
+              const uint64_t o = kk * 2;                 // 32 bytes (16 BF16 of K) per instruction
+              // level p + q starts at its first pair (p = 0)
+              mma_desc<0>(acc, ap + o, bq + o, IDESC, (p == 0 && kk == 0) ? 0u : 1u);
+              mma_desc<0>(acc, aq + o, bq + (2 * BNC * ROW >> 4) + o, IDESC, 1u);
             }
           }
         }
@@ -234,35 +190,53 @@ __global__ void __launch_bounds__(192, 1) k_herk_emu(Args args, const __grid_con
     }
   } else {
     // epilogue: lane = row r; A[r][c] -= 2^(e_r + e_c - 16) * (sum of the levels)
-    const int row = warp * 32 + lane;
+    const int quarter = warp & 3, cw = (warp >> 2) * EPI_COLS;   // lanes 32 quarter.., columns cw..
+    static_assert(EPI_WARPS % 4 == 0 && EPI_COLS % 4 == 0, "epilogue split");
+    const int row = quarter * 32 + lane;
     const int r = r0 + row;
+    double2* A = args.A[m];
+    const int* ex = args.ex[m];
+    // lane = row r; GC columns per group.  Loads of A and of the column exponents are issued a
+    // group ahead of the stores (a store to A would otherwise order every later load of A behind
+    // it), the first group while the MMAs run.
+    constexpr int GC = 4;
+    double2 av[GC];
+    int ec[GC];
+    auto load_group = [&](int cg) {
+#pragma unroll
+      for (int e = 0; e < GC; ++e) {
+        const int c = c0 + cw + cg + e;
+        const bool in = r < N && c < N && c <= r;
+        av[e] = in ? A[(size_t)r * N + c] : make_double2(0.0, 0.0);
+        ec[e] = in ? ex[c] : 0;
+      }
+    };
+    load_group(0);
+    const int er = r < N ? ex[r] : 0;
     const bool ok = mbar_wait(acc_full, 0u, abort_flag, args.status) && !*abort_flag;
     uint32_t all_ok;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(all_ok)
-        : "r"((uint32_t)ok)
+        : "r"((uint32_t)ok), "n"(EPI_WARPS * 32)
         : "memory");
     if (all_ok) {
       fence_after();
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-      const int er = r < N ? args.ex[m][r] : 0;
-      double2* A = args.A[m];
+      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + cw;
 #pragma unroll 1
-      for (int c8 = 0; c8 < BNC; c8 += 8) {
-        float v[NLEV][2][8];
+      for (int cg = 0; cg < EPI_COLS; cg += GC) {
+        float v[NLEV][2][GC];
 #pragma unroll
         for (int lv = 0; lv < NLEV; ++lv) {
-          tmem_ld8(lane_base + lv * ACC + c8, v[lv][0]);
-          tmem_ld8(lane_base + lv * ACC + BNC + c8, v[lv][1]);
+          tmem_ld4(lane_base + lv * ACC + cg, v[lv][0]);
+          tmem_ld4(lane_base + lv * ACC + BNC + cg, v[lv][1]);
         }
         tmem_wait_ld();
+        double2 out[GC];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int c = c0 + c8 + e;
-          if (r >= N || c >= N || c > r) continue;
-          const int sh = er + args.ex[m][c] - 2 * BETA;
+        for (int e = 0; e < GC; ++e) {
+          const int sh = er + ec[e] - 2 * BETA;
           // the exact level sums, smallest first
           df re = two_sum(v[NLEV - 1][0][e], v[NLEV - 2][0][e]);
           df im = two_sum(v[NLEV - 1][1][e], v[NLEV - 2][1][e]);
@@ -272,25 +246,26 @@ __global__ void __launch_bounds__(192, 1) k_herk_emu(Args args, const __grid_con
             im = df_add_f(im, v[lv][1][e]);
           }
           // hi + lo is exact in FP64 (48 bits), so A - (hi + lo) rounds once
-          const double dr = f32_scaled(re.h, sh) + f32_scaled(re.l, sh);
-          const double di = f32_scaled(im.h, sh) + f32_scaled(im.l, sh);
-          double2* pa = A + (size_t)r * N + c;
-          double2 a = *pa;
-          a.x -= dr;
-          a.y -= di;
-          *pa = a;
+          out[e].x = av[e].x - (f32_scaled(re.h, sh) + f32_scaled(re.l, sh));
+          out[e].y = av[e].y - (f32_scaled(im.h, sh) + f32_scaled(im.l, sh));
+        }
+        if (cg + GC < EPI_COLS) load_group(cg + GC);
+#pragma unroll
+        for (int e = 0; e < GC; ++e) {
+          const int c = c0 + cw + cg + e;
+          if (r < N && c < N && c <= r) A[(size_t)r * N + c] = out[e];
         }
       }
     }
   }
   __syncthreads();
-  if (warp == 5 && lane == 0) {
+  if (warp == MMA_WARP && lane == 0) {
     // an epilogue that gave up early leaves MMAs in flight: let them retire before the dealloc
     const unsigned long long t0 = gtime();
     while (!mbar_test(drain, 0u) && gtime() - t0 < WAIT_NS) {
     }
   }
-  if (warp == 4 && lane == 0 && *abort_flag) {
+  if (warp == TMA_WARP && lane == 0 && *abort_flag) {
     // a TMA load that may still be landing: wait (bounded) for the stage's phase
     const unsigned long long t0 = gtime();
     while (!mbar_test(full, 0u) && gtime() - t0 < WAIT_NS) {
@@ -337,42 +312,53 @@ size_t herk_emu_scratch_bytes(int N) {
   return 2 * per;
 }
 
+EmuPlanes herk_emu_planes(int N, void* scratch) {
+  using namespace hemu;
+  EmuPlanes e;
+  e.rpad = rpad_for(N);
+  const size_t planes_b = ((size_t)DIG * PLANES * e.rpad * NB * 2 + 1023) / 1024 * 1024;
+  const size_t ex_b = ((size_t)e.rpad * 4 + 1023) / 1024 * 1024;
+  char* p = (char*)scratch;
+  for (int m = 0; m < 2; ++m) {
+    e.planes[m] = p; p += planes_b;
+    e.ex[m] = (int*)p; p += ex_b;
+  }
+  return e;
+}
+
 bool launch_herk_emu(int N, int jb, double2* const* A, int nbatch, void* scratch, size_t bytes,
-                     int* status, cudaStream_t s) {
+                     bool digits_done, int* status, cudaStream_t s) {
   using namespace hemu;
   const int R0 = (jb + 1) * NB;
   const int R = N - R0;
   if (R <= 0) return true;
   if (!scratch || bytes < herk_emu_scratch_bytes(N)) return false;
-  const int rp = rpad_for(N);
-  const size_t planes_b = ((size_t)DIG * PLANES * rp * NB * 2 + 1023) / 1024 * 1024;
-  const size_t ex_b = ((size_t)rp * 4 + 1023) / 1024 * 1024;
-  char* p = (char*)scratch;
-  __nv_bfloat16* pl[2];
-  int* ex[2];
-  for (int m = 0; m < 2; ++m) {
-    pl[m] = (__nv_bfloat16*)p; p += planes_b;
-    ex[m] = (int*)p; p += ex_b;
-  }
+  const EmuPlanes e = herk_emu_planes(N, scratch);
+  const int rp = e.rpad;
   const int nb = nbatch > 1 ? 2 : 1;
-  k_panel_digits<<<dim3((R + 7) / 8, nb), 256, 0, s>>>(A[0], nb > 1 ? A[1] : A[0], N, jb, rp, pl[0],
-                                                        pl[1], ex[0], ex[1]);
   Maps maps;
   for (int m = 0; m < 2; ++m) {
     const int k = m < nb ? m : 0;
     const size_t rows = (size_t)DIG * PLANES * rp;
-    if (!make_map(&maps.a[m], pl[k], rows, BM) || !make_map(&maps.b[m], pl[k], rows, BNC)) return false;
+    if (!make_map(&maps.a[m], e.planes[k], rows, BM) || !make_map(&maps.b[m], e.planes[k], rows, BNC))
+      return false;
   }
+  if (!digits_done)
+    k_panel_digits<<<dim3((R + 7) / 8, nb), 256, 0, s>>>(
+        A[0], nb > 1 ? A[1] : A[0], N, jb, rp, (__nv_bfloat16*)e.planes[0],
+        (__nv_bfloat16*)e.planes[1], e.ex[0], e.ex[1]);
   Args a;
   a.A[0] = A[0];
   a.A[1] = nb > 1 ? A[1] : A[0];
-  a.ex[0] = ex[0];
-  a.ex[1] = nb > 1 ? ex[1] : ex[0];
+  a.ex[0] = e.ex[0];
+  a.ex[1] = nb > 1 ? e.ex[1] : e.ex[0];
   a.N = N; a.R0 = R0; a.rpad = rp;
   a.nI = (R + BM - 1) / BM;
   a.nJ = (R + BNC - 1) / BNC;
   a.status = status;
-  k_herk_emu<<<dim3(a.nI, a.nJ, nb), 192, SMEM_BYTES, s>>>(a, maps);
+  int tiles = 0;
+  for (int I = 0; I < a.nI; ++I) tiles += std::min((BM / BNC) * (I + 1), a.nJ);
+  k_herk_emu<<<dim3(tiles, nb), EMU_THREADS, SMEM_BYTES, s>>>(a, maps);
   return true;
 }
 

@@ -8,6 +8,7 @@
 // of k_linalg_df.cu.
 #include <cuda_runtime.h>
 
+#include "herk_digits.cuh"
 #include "icwf_internal.h"
 #include "k_common.cuh"
 
@@ -52,20 +53,41 @@ struct MatBatch { double2* m[2]; double* inv[2]; double2* D[2]; };
 constexpr int PF_THREADS = 256;
 
 
-// Factor the diagonal block jb of each matrix (one CTA per matrix) in FP64.  Column c:
-// y = 1/sqrt(A_cc), L_cc = A_cc y; the trailing triangle takes the rank-1 update
-// A_rq -= A_rc conj(A_qc) y^2 from the unscaled column, which is scaled (L_rc = A_rc y) one column
-// later, when nothing reads it any more.  Thread 0 updates the next pivot first (pair (c+1, c+1))
-// and computes its reciprocal square root while the other threads finish the rank-1 update, so
-// each column needs a single barrier.  Outputs: L in place and the reciprocal pivots.  Rows and
-// columns beyond N are treated as identity so that ragged sizes factor cleanly.
-__device__ __forceinline__ double rsqrt_ieee(double d) { return 1.0 / sqrt(d); }
+// Factor the diagonal block jb of each matrix (one CTA per matrix) in FP64, right-looking by
+// columns.  Column c: its entries below the pivot are scaled, L_rc = A_rc y_c (y_c = 1/sqrt(A_cc),
+// computed during the previous column); then the trailing triangle takes the rank-1 update
+// A_rq -= L_rc conj(L_qc) for c < q <= r (four FMAs per element).  The update's pairs are read
+// from a table sorted by q descending, so those of column c are its first (31-c)(32-c)/2 entries
+// and every warp instruction of the update runs on full warps (FP64 instructions issue per warp,
+// whatever the number of active lanes).  Thread 0 updates the next pivot, A_{c+1,c+1}, itself and
+// computes its reciprocal square root while the others finish the update.  Two barriers per
+// column.  Outputs: L in place and the reciprocal pivots.  Rows and columns beyond N are treated
+// as identity so that ragged sizes factor cleanly.
+//
+// The reciprocal square root of a pivot starts from the FP32 estimate and takes two Newton steps
+// y <- y (3 - d y^2) / 2 in FP64 (each squares the relative error: 2^-22 -> 2^-43 -> FP64
+// rounding), a shorter dependent chain than an FP64 square root followed by a division.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);   // outside the FP32 estimate's range
+  double y = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = y * fma(-0.5 * d, y * y, 1.5);
+  return y;
+}
 __device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) { return cmul(a, cconj(b)); }
+// a -= t conj(b) in four FMAs
+__device__ __forceinline__ double2 csub_mul_conj(double2 a, double2 t, double2 b) {
+  a.x = fma(-t.x, b.x, fma(-t.y, b.y, a.x));
+  a.y = fma(-t.y, b.x, fma(t.x, b.y, a.y));
+  return a;
+}
+
+constexpr int PF_PAIRS = (NB - 1) * NB / 2;   // pairs (r, q), 1 <= q <= r <= 31
 
 __global__ void __launch_bounds__(PF_THREADS) k_potrf_diag(int N, MatBatch mb, int jb, int* status) {
   __shared__ double2 L[NB][NB + 1];
   __shared__ double yv[NB];
-  __shared__ double y2b[2];   // y^2 of the current column, double-buffered by column parity
+  __shared__ unsigned char pr[PF_PAIRS], pq[PF_PAIRS];
   double2* A = mb.m[blockIdx.y];
   double* inv = mb.inv[blockIdx.y];
   const int r0 = jb * NB;
@@ -75,36 +97,42 @@ __global__ void __launch_bounds__(PF_THREADS) k_potrf_diag(int N, MatBatch mb, i
     if (c <= r && r0 + r < N && r0 + c < N) v = A[(size_t)(r0 + r) * N + r0 + c];
     L[r][c] = v;
   }
+  // pair table: q = 31, 30, ..., 1, and r = q..31 within each q
+  for (int i = threadIdx.x; i < PF_PAIRS; i += PF_THREADS) {
+    int q = NB - 1, k = i;
+    while (k >= NB - q) { k -= NB - q; --q; }
+    pr[i] = (unsigned char)(q + k);
+    pq[i] = (unsigned char)q;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double d = L[0][0].x;
     if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
-    const double y = rsqrt_ieee(d);
+    const double y = rsqrt_newton(d);
     L[0][0] = make_double2(d * y, 0.0);
     yv[0] = y;
-    y2b[0] = y * y;
   }
   __syncthreads();
-  for (int c = 0; c < NB; ++c) {
-    if (c > 0) {
-      // column c-1 is no longer read: scale it now
-      const int r = c + (int)threadIdx.x;
-      if (r < NB) L[r][c - 1] = cscale(L[r][c - 1], yv[c - 1]);
+  for (int c = 0; c < NB - 1; ++c) {
+    {
+      const int r = c + 1 + (int)threadIdx.x;
+      if (r < NB) L[r][c] = cscale(L[r][c], yv[c]);
     }
-    const double y2 = y2b[c & 1];
-    // lower-triangle pairs c < q <= r: thread t takes row c + 1 + t/8 and every 8th column
-    const int r = c + 1 + (int)(threadIdx.x >> 3);
-    for (int q = c + 1 + (int)(threadIdx.x & 7); r < NB && q <= r; q += 8) {
-      L[r][q] = csub(L[r][q], cscale(cmul_conj(L[r][c], L[q][c]), y2));
-      if (threadIdx.x == 0) {
-        // thread 0 just produced the pivot of column c + 1
-        double d = L[c + 1][c + 1].x;
-        if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
-        const double y = rsqrt_ieee(d);
-        L[c + 1][c + 1] = make_double2(d * y, 0.0);
-        yv[c + 1] = y;
-        y2b[(c + 1) & 1] = y * y;
-      }
+    __syncthreads();
+    const int n = (NB - 1 - c) * (NB - c) / 2;
+    const int skip = n - (NB - 1 - c);   // the pair (c+1, c+1): thread 0's
+    if (threadIdx.x == 0) {
+      const double2 l = L[c + 1][c];
+      double d = L[c + 1][c + 1].x - (l.x * l.x + l.y * l.y);
+      if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
+      const double y = rsqrt_newton(d);
+      L[c + 1][c + 1] = make_double2(d * y, 0.0);
+      yv[c + 1] = y;
+    }
+    for (int i = (int)threadIdx.x; i < n; i += PF_THREADS) {
+      if (i == skip) continue;
+      const int r = pr[i], q = pq[i];
+      L[r][q] = csub_mul_conj(L[r][q], L[r][c], L[q][c]);
     }
     __syncthreads();
   }
@@ -118,36 +146,44 @@ __global__ void __launch_bounds__(PF_THREADS) k_potrf_diag(int N, MatBatch mb, i
 constexpr int TR_WARPS = 8;   // rows per panel-solve CTA
 
 // Panel solve A_ib <- A_ib L_bb^-H below the diagonal block jb in FP64: one warp per row, lane =
-// column, column-oriented substitution x_m = a_m / L_mm, a_c -= x_m conj(L_cm) (c > m).
-__global__ void __launch_bounds__(TR_WARPS * 32) k_trsm_panel(int N, MatBatch mb, int jb) {
-  __shared__ double2 Ls[NB][NB + 1];
-  __shared__ double ys[NB];
-  double2* A = mb.m[blockIdx.y];
-  const double* inv = mb.inv[blockIdx.y];
+// column, column-oriented substitution on unscaled numerators: a_c -= a_m (conj(L_cm) / L_mm)
+// for c > m with the multipliers conj(L_cm) / L_mm staged in shared memory (four FMAs per
+// update), and x_c = a_c / L_cc once at the end.  With `emu`, the finished row's digit planes for
+// the emulated trailing update are written as well.
+__global__ void __launch_bounds__(TR_WARPS * 32) k_trsm_panel(int N, MatBatch mb, int jb,
+                                                              EmuPlanes emu) {
+  __shared__ double2 Lp[NB][NB + 1];
+  const int bm = blockIdx.y;
+  double2* A = mb.m[bm];
+  const double* inv = mb.inv[bm];
   const int c0 = jb * NB;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
     double2 l = make_double2(0.0, 0.0);
-    if (c < r && c0 + r < N && c0 + c < N) l = A[(size_t)(c0 + r) * N + c0 + c];
-    Ls[r][c] = l;
+    if (c < r && c0 + r < N) l = cscale(cconj(A[(size_t)(c0 + r) * N + c0 + c]), inv[c0 + c]);
+    Lp[r][c] = l;
   }
-  if (threadIdx.x < NB) ys[threadIdx.x] = (c0 + threadIdx.x < N) ? inv[c0 + threadIdx.x] : 1.0;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = (jb + 1) * NB + blockIdx.x * TR_WARPS + warp;
   if (row >= N) return;
-  const bool cok = c0 + lane < N;
-  double2 a = cok ? A[(size_t)row * N + c0 + lane] : make_double2(0.0, 0.0);
-#pragma unroll 4
-  for (int m = 0; m < NB; ++m) {
-    const double2 xs = cscale(a, ys[m]);
-    double2 x;
-    x.x = __shfl_sync(0xffffffffu, xs.x, m);
-    x.y = __shfl_sync(0xffffffffu, xs.y, m);
-    if (lane == m) a = x;
-    else if (lane > m) a = csub(a, cmul_conj(x, Ls[lane][m]));
+  // a block column with rows below it is full: every lane's column is inside the matrix
+  double2 a = A[(size_t)row * N + c0 + lane];
+#pragma unroll
+  for (int m = 0; m < NB - 1; ++m) {
+    double2 am;
+    am.x = __shfl_sync(0xffffffffu, a.x, m);
+    am.y = __shfl_sync(0xffffffffu, a.y, m);
+    if (lane > m) {
+      const double2 l = Lp[lane][m];
+      a.x = fma(-am.x, l.x, fma(am.y, l.y, a.x));
+      a.y = fma(-am.x, l.y, fma(-am.y, l.x, a.y));
+    }
   }
-  if (cok) A[(size_t)row * N + c0 + lane] = a;
+  a = cscale(a, inv[c0 + lane]);
+  A[(size_t)row * N + c0 + lane] = a;
+  if (emu.planes[0])
+    hemu::emit_row_digits(a, row, lane, emu.rpad, (__nv_bfloat16*)emu.planes[bm], emu.ex[bm]);
 }
 
 // Inverse of every diagonal block after the factorisation: D_b = L_bb^-1 (lower triangular),
@@ -263,6 +299,10 @@ int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const
   mb.D[0] = D[0];
   mb.D[1] = nbatch > 1 ? D[1] : D[0];
   const int T = (N + NB - 1) / NB;
+  // the panel solve writes the emulated update's digit planes (scratch checked here, so that a
+  // launch_herk_emu refusal cannot leave a panel without its FP64 update)
+  EmuPlanes emu{};
+  if (emu_scratch && emu_bytes >= herk_emu_scratch_bytes(N)) emu = herk_emu_planes(N, emu_scratch);
   int launches = 0;
   for (int jb = 0; jb < T; ++jb) {
     k_potrf_diag<<<dim3(1, nbatch), PF_THREADS, 0, s>>>(N, mb, jb, status);
@@ -270,13 +310,11 @@ int launch_cholesky(int N, double2* const* A, double* const* inv, double2* const
     const int rest = T - jb - 1;
     if (rest > 0) {
       const int rows = N - (jb + 1) * NB;
-      k_trsm_panel<<<dim3((rows + TR_WARPS - 1) / TR_WARPS, nbatch), TR_WARPS * 32, 0, s>>>(N, mb, jb);
-      if (emu_scratch && launch_herk_emu(N, jb, A, nbatch, emu_scratch, emu_bytes, status, s)) {
-        launches += 3;
-      } else {
+      k_trsm_panel<<<dim3((rows + TR_WARPS - 1) / TR_WARPS, nbatch), TR_WARPS * 32, 0, s>>>(
+          N, mb, jb, emu);
+      if (!emu.planes[0] || !launch_herk_emu(N, jb, A, nbatch, emu_scratch, emu_bytes, true, status, s))
         k_herk_update<<<dim3(rest * (rest + 1) / 2, nbatch), 256, 0, s>>>(N, mb, jb);
-        launches += 2;
-      }
+      launches += 2;
     }
   }
   k_trtri_diag<<<dim3(T, nbatch), 128, 0, s>>>(N, mb);
