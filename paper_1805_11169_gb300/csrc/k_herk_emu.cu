@@ -15,8 +15,9 @@
 // together stay below 2^-47 of 2^(e_r + e_c).  A level's sum over K = 32 (64 real products of
 // at most 2^15 units each, at most 9 pairs) stays below 2^24 units, so each of the seven kept
 // levels is accumulated EXACTLY in its own FP32 accumulator in TMEM.  The epilogue adds the seven
-// in double-float arithmetic from the smallest level up (about 2^-48 of the result), scales by
-// 2^(e_r + e_c - 16) with integer exponent arithmetic and subtracts the result from A in FP64.
+// from the smallest level up, the two smallest in FP32 and the rest in double-float arithmetic
+// (about 2^-48 of the result), scales by 2^(e_r + e_c - 16) with integer exponent arithmetic and
+// subtracts the result from A in FP64.
 //
 // Complex products on real MMAs: with P/Q the real/imaginary planes,
 //   [Re | Im] += P_r [P_c | -Q_c] + Q_r [Q_c | P_c]
@@ -28,8 +29,8 @@
 // lower triangle, 576 threads; warp 16 loads the whole K = 32 slice of all digit planes with TMA
 // (64-byte rows and swizzle, one stage, 168 KB), warp 17 issues the 112 MMAs, warps 0..15 run the
 // epilogue (warp w reads TMEM lanes 32 (w mod 4).. and columns 8 (w div 4)..: four warps per SM
-// sub-partition hide each other's dependent chains).  Waits are bounded (2 s): a timeout raises the status flag, drains what is in flight
-// and returns.
+// sub-partition hide each other's dependent chains).  Waits are bounded (2 s): a timeout raises
+// the status flag, drains what is in flight and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1) k_herk_emu(Args args, const __
   uint64_t* drain = full + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  int* ecol = (int*)(tmem_slot + 2);   // exponents of this tile's 32 columns
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = args.N, R0 = args.R0, rpad = args.rpad;
   const int r0 = R0 + I * BM, c0 = R0 + J * BNC;
@@ -201,18 +203,17 @@ __global__ void __launch_bounds__(EMU_THREADS, 1) k_herk_emu(Args args, const __
     // it), the first group while the MMAs run.
     constexpr int GC = 4;
     double2 av[GC];
-    int ec[GC];
     auto load_group = [&](int cg) {
 #pragma unroll
       for (int e = 0; e < GC; ++e) {
         const int c = c0 + cw + cg + e;
         const bool in = r < N && c < N && c <= r;
         av[e] = in ? A[(size_t)r * N + c] : make_double2(0.0, 0.0);
-        ec[e] = in ? ex[c] : 0;
       }
     };
     load_group(0);
     const int er = r < N ? ex[r] : 0;
+    if (warp == 0) ecol[lane] = c0 + lane < N ? ex[c0 + lane] : 0;   // read after the barrier
     const bool ok = mbar_wait(acc_full, 0u, abort_flag, args.status) && !*abort_flag;
     uint32_t all_ok;
     asm volatile(
@@ -236,12 +237,13 @@ __global__ void __launch_bounds__(EMU_THREADS, 1) k_herk_emu(Args args, const __
         double2 out[GC];
 #pragma unroll
         for (int e = 0; e < GC; ++e) {
-          const int sh = er + ec[e] - 2 * BETA;
-          // the exact level sums, smallest first
-          df re = two_sum(v[NLEV - 1][0][e], v[NLEV - 2][0][e]);
-          df im = two_sum(v[NLEV - 1][1][e], v[NLEV - 2][1][e]);
+          const int sh = er + ecol[cw + cg + e] - 2 * BETA;
+          // the exact level sums, smallest first; the two smallest (below 2^-16 units of level 0)
+          // are added in FP32 (rounding below 2^-40 units)
+          df re = two_sum(__fadd_rn(v[NLEV - 1][0][e], v[NLEV - 2][0][e]), v[NLEV - 3][0][e]);
+          df im = two_sum(__fadd_rn(v[NLEV - 1][1][e], v[NLEV - 2][1][e]), v[NLEV - 3][1][e]);
 #pragma unroll
-          for (int lv = NLEV - 3; lv >= 0; --lv) {
+          for (int lv = NLEV - 4; lv >= 0; --lv) {
             re = df_add_f(re, v[lv][0][e]);
             im = df_add_f(im, v[lv][1][e]);
           }

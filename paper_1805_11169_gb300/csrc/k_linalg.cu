@@ -64,15 +64,29 @@ constexpr int PF_THREADS = 256;
 // column.  Outputs: L in place and the reciprocal pivots.  Rows and columns beyond N are treated
 // as identity so that ragged sizes factor cleanly.
 //
-// The reciprocal square root of a pivot starts from the FP32 estimate and takes two Newton steps
-// y <- y (3 - d y^2) / 2 in FP64 (each squares the relative error: 2^-22 -> 2^-43 -> FP64
-// rounding), a shorter dependent chain than an FP64 square root followed by a division.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);   // outside the FP32 estimate's range
-  double y = (double)rsqrtf((float)d);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) y = y * fma(-0.5 * d, y * y, 1.5);
-  return y;
+// FP64 operations wait for one another for a long time on this GPU, so the pivot chain is kept
+// short.  The reciprocal square root of a pivot d starts from the FP32 estimate (d narrowed and
+// the estimate widened by integer operations on the bit patterns: no FP64 instruction) and takes
+// one third-order correction in FP64, y = y0 (1 + r/2 + 3 r^2/8) with r = 1 - d y0^2 (the
+// binomial series of (1 - r)^(-1/2) cut after r^2): the estimate's ~2^-22 relative error becomes
+// ~2^-64, below FP64 rounding, in five dependent FP64 operations.
+__device__ __forceinline__ double rsqrt_fp64(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)(u >> 52);   // d > 0
+  if (E < 1023 - 120 || E > 1023 + 120) return 1.0 / sqrt(d);   // outside FP32's range
+  // d with its mantissa truncated to 23 bits, as an FP32 number (relative error < 2^-23)
+  const float f = __uint_as_float(((uint32_t)(E - 1023 + 127) << 23) | (uint32_t)((u >> 29) & 0x7FFFFFu));
+  const uint32_t v = __float_as_uint(rsqrtf(f));
+  // exact widening of the estimate
+  const double y0 = __hiloint2double(
+      (int)(((((v >> 23) & 0xFFu) - 127u + 1023u) << 20) | ((v & 0x7FFFFFu) >> 3)), (int)((v & 7u) << 29));
+  const double r = fma(-d, y0 * y0, 1.0);
+  return fma(y0, r * fma(0.375, r, 0.5), y0);
+}
+// a pivot is usable when 0 < d < inf (integer test on the bits: no FP64 compare on the chain)
+__device__ __forceinline__ bool pivot_ok(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0 && b < 0x7FF0000000000000ll;
 }
 __device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) { return cmul(a, cconj(b)); }
 // a -= t conj(b) in four FMAs
@@ -107,25 +121,25 @@ __global__ void __launch_bounds__(PF_THREADS) k_potrf_diag(int N, MatBatch mb, i
   __syncthreads();
   if (threadIdx.x == 0) {
     double d = L[0][0].x;
-    if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
-    const double y = rsqrt_newton(d);
+    if (!pivot_ok(d)) { set_flag(status, ST_CHOL); d = 1.0; }
+    const double y = rsqrt_fp64(d);
     L[0][0] = make_double2(d * y, 0.0);
     yv[0] = y;
   }
   __syncthreads();
   for (int c = 0; c < NB - 1; ++c) {
+    double2 l0;   // thread 0: L_{c+1,c}, kept in registers for the next pivot
     {
       const int r = c + 1 + (int)threadIdx.x;
-      if (r < NB) L[r][c] = cscale(L[r][c], yv[c]);
+      if (r < NB) L[r][c] = l0 = cscale(L[r][c], yv[c]);
     }
     __syncthreads();
     const int n = (NB - 1 - c) * (NB - c) / 2;
     const int skip = n - (NB - 1 - c);   // the pair (c+1, c+1): thread 0's
     if (threadIdx.x == 0) {
-      const double2 l = L[c + 1][c];
-      double d = L[c + 1][c + 1].x - (l.x * l.x + l.y * l.y);
-      if (!(d > 0.0)) { set_flag(status, ST_CHOL); d = 1.0; }
-      const double y = rsqrt_newton(d);
+      double d = fma(-l0.x, l0.x, fma(-l0.y, l0.y, L[c + 1][c + 1].x));
+      if (!pivot_ok(d)) { set_flag(status, ST_CHOL); d = 1.0; }
+      const double y = rsqrt_fp64(d);
       L[c + 1][c + 1] = make_double2(d * y, 0.0);
       yv[c + 1] = y;
     }
