@@ -43,7 +43,7 @@ DF64_TFLOPS = FP32_LANE_OPS * 8 / DF64_CMAC_OPS / 1e12
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
 # DRAM bytes (read + write) per family call from one ncu capture, with the profile that gives them;
 # keyed by (family, mode, N).  Valid only while the kernels are the ones profiled.
-TRAFFIC = {("cholesky", "tf32x3", 1024): (193.2e6, "profiles/k_chol_step_df_mixed_N1024.md")}
+TRAFFIC = {("cholesky", "tf32x3", 1024): (193.6e6, "profiles/k_chol_step_df_mixed_N1024.md")}
 
 
 def parse():

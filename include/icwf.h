@@ -80,8 +80,9 @@ typedef struct {
                                factorisations per step); 1: S, Heff frozen at t_n (one) */
   int32_t max_rank;         /* upper bound on the kept rank k (0: no bound beyond the cutoff) */
   int32_t solve_fp64;       /* mixed modes only: 1 runs the Cholesky factorisations and triangular
-                               solves in FP64 (as ICWF_FP64 does) instead of double-float;
-                               ignored by ICWF_FP64 */
+                               solves with the FP64 solver (as ICWF_FP64 does; its trailing
+                               updates in emulated FP64, see icwf_set_emulated_update) instead of
+                               double-float; ignored by ICWF_FP64 */
   int32_t overlap_split;    /* mixed modes only: 0 (default) computes S = S1 o S2 as exact Grams
                                of the CWFs in a 4-digit fixed-point form on the tensor cores, so
                                S is positive semidefinite to FP64 rounding and eps can be as

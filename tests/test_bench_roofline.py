@@ -24,7 +24,7 @@ def test_cholesky_two_matrices_per_call():
     assert r["kernel"] == "cholesky" and r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(2 * 4 / 3 * 1024 ** 3 / 1.3e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.DF64_TFLOPS)
-    assert r["traffic"] == pytest.approx(193.2e6)
+    assert r["traffic"] == pytest.approx(193.6e6)
     frozen = bench.roofline({"cholesky": (130.0, 100)}, W, 15, "tf32x3", PEAKS, "df64", 1)
     assert frozen["achieved"] == pytest.approx(r["achieved"] / 2)
 
