@@ -756,13 +756,14 @@ def _make_job(lib, job, precision):
     return sim, w
 
 
-def _run_stream(lib, jobs, arrivals, graphs, max_live, precision):
+def _run_stream(lib, jobs, arrivals, graphs, max_live, precision, grouping=True):
     """Feed the jobs at their arrival times into a pool and tick it until all are done."""
     import numpy as np
     import paper_1805_11169_gb300 as g
     n_jobs = len(jobs)
     pool = g.icwf_pool_create(64 << 30, max_live)
     g.icwf_pool_set_graphs(pool, graphs)
+    g.icwf_pool_set_grouping(pool, grouping, 0)
     t_start = time.perf_counter()
     submitted, lat, ids, grids, results = 0, {}, {}, {}, {}
     done = set()
@@ -798,6 +799,8 @@ def _run_stream(lib, jobs, arrivals, graphs, max_live, precision):
             "graph_builds": stats["graph_builds"],
             "kernels_per_graph_launch": (stats["kernel_nodes"] / stats["graph_launches"]
                                          if stats["graph_launches"] else None),
+            "grouped_kernels_per_graph_launch": (stats["group_nodes"] / stats["graph_launches"]
+                                                 if stats["graph_launches"] else None),
             "host_launches_per_tick": (stats["graph_launches"] / stats["ticks"] if graphs else
                                        None),
             "eager_job_steps": stats["eager_job_steps"]}, results
@@ -805,7 +808,8 @@ def _run_stream(lib, jobs, arrivals, graphs, max_live, precision):
 
 def run_serving(n_jobs, mode="tf32x3", seed=0, load=0.7, max_live=16, n_checked=4):
     """Poisson stream of mixed-size jobs (N up to 2048) through the pool (continuous batching),
-    once with captured tick graphs (the default) and once with direct launches: job latency
+    with captured tick graphs and grouped velocity/propagation kernels over all live jobs (the
+    default), with tick graphs of per-job kernels only, and with direct launches: job latency
     p50/p99 (arrival -> result on the host), aggregate trajectory-steps/s and launches per tick.
     Jobs' mixed-precision results are checked against FP64 runs of the same jobs (a sample of the
     small ones: the FP64 path is ~50x slower)."""
@@ -826,6 +830,7 @@ def run_serving(n_jobs, mode="tf32x3", seed=0, load=0.7, max_live=16, n_checked=
     rate = load / mean_service
     arrivals = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / rate, n_jobs))
     graphs, res = _run_stream(lib, jobs, arrivals, True, max_live, prec)
+    ungrouped, _ = _run_stream(lib, jobs, arrivals, True, max_live, prec, grouping=False)
     eager, _ = _run_stream(lib, jobs, arrivals, False, max_live, prec)
     # precision check: the first n_checked jobs with N <= 256, in FP64, same seed, alone
     checks = []
@@ -845,7 +850,8 @@ def run_serving(n_jobs, mode="tf32x3", seed=0, load=0.7, max_live=16, n_checked=
                        "rho_R_L1": float(w.dR * np.sum(np.abs(ob["rho_R"] - ref["rho_R"]))),
                        "pop_L1": float(np.sum(np.abs(ob["pop"] - ref["pop"])))})
     return {"jobs": n_jobs, "p50_s": graphs["p50_s"], "p99_s": graphs["p99_s"],
-            "traj_steps_per_s": graphs["traj_steps_per_s"], "graphs": graphs, "eager": eager,
+            "traj_steps_per_s": graphs["traj_steps_per_s"], "graphs": graphs,
+            "graphs_ungrouped": ungrouped, "eager": eager,
             "arrival_rate_per_s": rate, "max_live": max_live, "precision": MODES[mode][1],
             "vs_fp64": checks,
             "stream": "Poisson arrivals; Shin-Metiu (3 grids, dt 0.05, eps 1e-6) and cavity "

@@ -280,11 +280,15 @@ icwf_status icwf_observables_static(icwf_handle h, icwf_obs* out);
 
 /* A pool admits jobs while their summed device footprint stays within hbm_budget_bytes and at
  * most max_jobs are live; pending jobs wait in arrival order.  Every icwf_pool_tick advances
- * every live job by one step.  By default each job's step is captured into CUDA graphs at its
- * first tick (one per parity of its ping-pong matrix buffers) and the live jobs' step graphs run
- * as child graphs of one tick graph, instantiated once per live set and parity pattern and
- * launched with a single cudaGraphLaunch per tick; the jobs share no memory, so their kernels
- * overlap on the device.  Job handles are owned by the pool after submission. */
+ * every live job by one step.  By default each tick is one CUDA graph, instantiated once per live
+ * set and parity pattern and launched with a single cudaGraphLaunch: first the grouped kernels,
+ * one persistent velocity kernel (Eq. v1/v2 and the Euler positions) and one persistent
+ * propagation kernel (the CWF equations' Strang step) per CWF precision, each over every
+ * trajectory or CWF of every live job of that precision (a device table of the jobs; ragged N and
+ * grids); then every job's remaining step (assembly, factorisations, RK4), captured into CUDA
+ * graphs at the job's first tick (one per parity of its ping-pong matrix buffers) and added as
+ * child graphs.  The jobs share no memory, so their child graphs overlap on the device.  Job
+ * handles are owned by the pool after submission. */
 icwf_status icwf_pool_create(size_t hbm_budget_bytes, int32_t max_jobs, icwf_pool* out);
 
 /* Counters of a pool since creation. */
@@ -295,6 +299,7 @@ typedef struct {
   int64_t kernel_nodes;     /* kernels executed inside tick graphs */
   int64_t graph_job_steps;  /* job steps run inside tick graphs */
   int64_t eager_job_steps;  /* job steps launched directly (graphs off or capture failed) */
+  int64_t group_nodes;      /* grouped (all-job) kernels executed inside tick graphs */
 } icwf_pool_stats;
 
 icwf_status icwf_pool_get_stats(icwf_pool pool, icwf_pool_stats* out);
@@ -302,6 +307,14 @@ icwf_status icwf_pool_get_stats(icwf_pool pool, icwf_pool_stats* out);
 /* on = 0 launches every job's kernels directly on its own streams at each tick (no graphs);
  * on = 1 (default) uses the captured tick graphs. */
 icwf_status icwf_pool_set_graphs(icwf_pool pool, int32_t on);
+
+/* on = 1 (default): tick graphs run the live jobs' velocities and propagation as grouped kernels
+ * over all jobs (above); on = 0: every job's child graph holds its own velocity and propagation
+ * kernels.  max_ctas > 0 caps the CTAs of each grouped kernel (its CTAs then loop over more work
+ * items each, leaving SMs to the jobs' other kernels); 0 = one wave at full occupancy.  Results
+ * are the same either way (the grouped kernels run the per-job kernels' arithmetic).  Takes effect
+ * at the next tick (jobs' step graphs are recorded again when grouping changes). */
+icwf_status icwf_pool_set_grouping(icwf_pool pool, int32_t on, int32_t max_ctas);
 
 /* Hand an initialised job to the pool (the pool owns it from now on) to run n_steps steps.
  * *job_id identifies it in icwf_pool_poll. */

@@ -48,7 +48,8 @@ class icwf_info(ct.Structure):
 class icwf_pool_stats(ct.Structure):
     _fields_ = [("ticks", ct.c_int64), ("graph_launches", ct.c_int64),
                 ("graph_builds", ct.c_int64), ("kernel_nodes", ct.c_int64),
-                ("graph_job_steps", ct.c_int64), ("eager_job_steps", ct.c_int64)]
+                ("graph_job_steps", ct.c_int64), ("eager_job_steps", ct.c_int64),
+                ("group_nodes", ct.c_int64)]
 
 
 class icwf_obs(ct.Structure):
@@ -97,6 +98,7 @@ def _load():
         "icwf_pool_destroy": [H],
         "icwf_pool_get_stats": [H, P(icwf_pool_stats)],
         "icwf_pool_set_graphs": [H, ct.c_int32],
+        "icwf_pool_set_grouping": [H, ct.c_int32, ct.c_int32],
         "icwf_exact2d_create": [P(icwf_params), d, P(H)],
         "icwf_exact2d_set_state": [H, d],
         "icwf_exact2d_set_projectors": [H, ct.c_int32, d],
@@ -334,6 +336,10 @@ def icwf_pool_get_stats(pool) -> dict:
 
 def icwf_pool_set_graphs(pool, on: bool):
     _check(LIB.icwf_pool_set_graphs(pool, 1 if on else 0))
+
+
+def icwf_pool_set_grouping(pool, on: bool, max_ctas: int = 0):
+    _check(LIB.icwf_pool_set_grouping(pool, 1 if on else 0, max_ctas))
 
 
 def icwf_pool_destroy(pool):

@@ -119,6 +119,9 @@ struct icwf_ctx {
   double t = 0.0;
   int64_t launches = 0;   // kernels launched by icwf_step
   int prop_threads = 256; // CTA size of the CWF propagator (autotuned per shape at create)
+  // step_once leaves out the velocity and propagation kernels (a serving pool records the job's
+  // step this way when grouped kernels over all live jobs do that part of the step)
+  bool traj_grouped = false;
   int64_t version = 0;    // bumped by calls that change captured kernel arguments (eps)
   // icwf_step's captured step graphs (one per parity of the ping-pong buffers)
   bool step_graphs = true;
@@ -387,17 +390,19 @@ void step_once(icwf_ctx* h) {
     solve(h, Lc, Dc, h->y, h->kk[st], true, h->side);
   }
   cudaEventRecord(h->ev_join, h->side);
-  {
-    ProfScope ps(h, F_VELOCITY);
-    if (h->mixed) launch_velocity<float>(j, h->C, h->stream);
-    else launch_velocity<double>(j, h->C, h->stream);
-    h->launches += h->mixed ? 2 : 1;
-  }
-  {
-    ProfScope ps(h, F_PROPAGATE);
-    if (h->mixed) launch_propagate<float>(j, h->prop_threads, h->stream);
-    else launch_propagate<double>(j, h->prop_threads, h->stream);
-    h->launches += 1;
+  if (!h->traj_grouped) {
+    {
+      ProfScope ps(h, F_VELOCITY);
+      if (h->mixed) launch_velocity<float>(j, h->C, h->stream);
+      else launch_velocity<double>(j, h->C, h->stream);
+      h->launches += h->mixed ? 2 : 1;
+    }
+    {
+      ProfScope ps(h, F_PROPAGATE);
+      if (h->mixed) launch_propagate<float>(j, h->prop_threads, h->stream);
+      else launch_propagate<double>(j, h->prop_threads, h->stream);
+      h->launches += 1;
+    }
   }
   assemble(h, h->S[nxt], h->H[nxt]);
   if (frozen) {
@@ -1346,6 +1351,7 @@ struct PoolJob {
   // one captured step per ping-pong parity of the job's matrix buffers
   cudaGraph_t g[2] = {nullptr, nullptr};
   bool graphs_tried = false, graphs_ok = false;
+  bool grouped = false;   // graphs recorded without velocities and propagation (grouped kernels)
   int64_t kernels_per_step = 0;
   int64_t version = -1;   // handle version the graphs were captured at
 };
@@ -1358,17 +1364,30 @@ struct icwf_pool_ctx {
   std::deque<int> pending;
   std::vector<int> live;
   bool use_graphs = true;
+  bool use_groups = true;   // grouped velocity and propagation kernels inside the tick graphs
+  int group_ctas = 0;       // CTA cap of each grouped kernel (0: one wave at full occupancy)
   cudaStream_t stream = nullptr;
-  // instantiated tick graphs of the current live set, keyed by (job id, parity) of every job
-  std::map<std::vector<int64_t>, cudaGraphExec_t> ticks_cache;
+  // instantiated tick graphs of the current live set, keyed by (job id, parity) of every job; each
+  // with the device table of its grouped kernels (NULL without grouping)
+  struct TickExec {
+    cudaGraphExec_t exec = nullptr;
+    void* table = nullptr;
+    int64_t group_nodes = 0;
+  };
+  std::map<std::vector<int64_t>, TickExec> ticks_cache;
   std::vector<int> cache_live;   // the live set the cache belongs to
   icwf_pool_stats stats{};
 };
 
 namespace {
 
+// Called between ticks only (every tick ends with a synchronisation of the pool's stream), so no
+// cached graph or table is in use on the device.
 void clear_tick_cache(icwf_pool pool) {
-  for (auto& kv : pool->ticks_cache) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : pool->ticks_cache) {
+    cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.table) cudaFree(kv.second.table);
+  }
   pool->ticks_cache.clear();
 }
 
@@ -1379,13 +1398,87 @@ void destroy_job_graphs(PoolJob& j) {
 }
 
 // Capture one step of the job for each parity of its ping-pong buffers (two consecutive steps
-// recorded, not executed), then restore the host-side step state.  Returns false (and leaves the
-// job to eager stepping) if the capture fails.
-bool capture_job_graphs(PoolJob& pj) {
+// recorded, not executed), then restore the host-side step state; with `grouped` the recorded
+// step leaves out the velocities and the propagation, which the tick's grouped kernels run.
+// Returns false (and leaves the job to eager stepping) if the capture fails.
+bool capture_job_graphs(PoolJob& pj, bool grouped) {
+  pj.h->traj_grouped = grouped;
   const bool ok = capture_step(pj.h, pj.g, &pj.kernels_per_step);
+  pj.h->traj_grouped = false;
   pj.graphs_ok = ok;
+  pj.grouped = grouped;
   pj.version = pj.h->version;
   return ok;
+}
+
+// Instantiate the tick graph of the jobs `run` at their current parities: with `grouped`, one
+// persistent velocity kernel and one persistent propagation kernel per CWF precision over all of
+// those jobs (their entries in one device table), on which every job's recorded step (a child
+// graph) depends; else the child graphs alone.  False (nothing kept) on any failure.
+bool build_tick(icwf_pool pool, const std::vector<int>& run, bool grouped,
+                icwf_pool_ctx::TickExec* out) {
+  std::vector<GroupJob> tab[2];   // [0]: FP64 CWFs, [1]: complex64 CWFs
+  int traj[2] = {0, 0}, cwfs[2] = {0, 0}, nmax[2] = {0, 0}, thr[2] = {256, 256};
+  double work[2] = {0, 0};
+  if (grouped) {
+    for (int id : run) {
+      icwf_ctx* h = pool->jobs[id].h;
+      const int t = h->mixed ? 1 : 0;
+      GroupJob q = group_job(view(h), h->C);
+      q.traj0 = traj[t];
+      q.cwf0 = cwfs[t];
+      tab[t].push_back(q);
+      traj[t] += h->N;
+      cwfs[t] += 2 * h->N;
+      nmax[t] = std::max(nmax[t], std::max(h->nx, h->nR));
+      // CTA size: the autotuned one of the job with the most propagation work
+      const double wj = (double)h->N * (double)(h->nx + h->nR);
+      if (wj > work[t]) { work[t] = wj; thr[t] = h->prop_threads; }
+    }
+  }
+  const size_t n0 = tab[0].size(), n1 = tab[1].size();
+  void* table = nullptr;
+  if (n0 + n1 > 0) {
+    if (cudaMalloc(&table, (n0 + n1) * sizeof(GroupJob)) != cudaSuccess) { cudaGetLastError(); return false; }
+    bool ok = n0 == 0 || cudaMemcpy(table, tab[0].data(), n0 * sizeof(GroupJob),
+                                    cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && (n1 == 0 || cudaMemcpy((GroupJob*)table + n0, tab[1].data(), n1 * sizeof(GroupJob),
+                                      cudaMemcpyHostToDevice) == cudaSuccess);
+    if (!ok) { cudaFree(table); cudaGetLastError(); return false; }
+  }
+  cudaGraph_t tg = nullptr;
+  bool ok = cudaGraphCreate(&tg, 0) == cudaSuccess;
+  cudaGraphNode_t deps[2];
+  size_t nd = 0;
+  int64_t gnodes = 0;
+  if (ok && n0 > 0) {
+    ok = add_group_nodes<double>(tg, nullptr, 0, (const GroupJob*)table, (int)n0, traj[0], cwfs[0],
+                                 nmax[0], thr[0], pool->group_ctas, &deps[nd++]);
+    gnodes += 2;
+  }
+  if (ok && n1 > 0) {
+    ok = add_group_nodes<float>(tg, nullptr, 0, (const GroupJob*)table + n0, (int)n1, traj[1],
+                                cwfs[1], nmax[1], thr[1], pool->group_ctas, &deps[nd++]);
+    gnodes += 2;
+  }
+  for (size_t k = 0; ok && k < run.size(); ++k) {
+    PoolJob& j = pool->jobs[run[k]];
+    cudaGraphNode_t node;
+    ok = cudaGraphAddChildGraphNode(&node, tg, nd ? deps : nullptr, nd, j.g[j.h->cur]) == cudaSuccess;
+  }
+  cudaGraphExec_t exec = nullptr;
+  ok = ok && cudaGraphInstantiate(&exec, tg, 0) == cudaSuccess;
+  if (tg) cudaGraphDestroy(tg);
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (table) cudaFree(table);
+    cudaGetLastError();
+    return false;
+  }
+  out->exec = exec;
+  out->table = table;
+  out->group_nodes = gnodes;
+  return true;
 }
 
 }  // namespace
@@ -1407,6 +1500,15 @@ icwf_status icwf_pool_create(size_t hbm_budget_bytes, int32_t max_jobs, icwf_poo
 icwf_status icwf_pool_set_graphs(icwf_pool pool, int32_t on) {
   if (!pool) return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_set_graphs: NULL pool");
   pool->use_graphs = on != 0;
+  return ICWF_OK;
+}
+
+icwf_status icwf_pool_set_grouping(icwf_pool pool, int32_t on, int32_t max_ctas) {
+  if (!pool || max_ctas < 0)
+    return fail(nullptr, ICWF_ERR_ARG, "icwf_pool_set_grouping: invalid argument");
+  if ((on != 0) != pool->use_groups || max_ctas != pool->group_ctas) clear_tick_cache(pool);
+  pool->use_groups = on != 0;
+  pool->group_ctas = max_ctas;
   return ICWF_OK;
 }
 
@@ -1486,15 +1588,15 @@ icwf_status icwf_pool_tick(icwf_pool pool, int32_t* n_live, int32_t* n_finished)
   if (graphs) {
     for (int id : run) {
       PoolJob& j = pool->jobs[id];
-      if (j.graphs_tried && j.version != j.h->version) {
-        // captured kernel arguments are stale: record the job's step again
+      if (j.graphs_tried && (j.version != j.h->version || j.grouped != pool->use_groups)) {
+        // captured kernel arguments are stale, or the grouping changed: record the step again
         destroy_job_graphs(j);
         clear_tick_cache(pool);
         j.graphs_tried = false;
       }
       if (!j.graphs_tried) {
         j.graphs_tried = true;
-        capture_job_graphs(j);
+        capture_job_graphs(j, pool->use_groups);
       }
       graphs = graphs && j.graphs_ok;
     }
@@ -1503,31 +1605,19 @@ icwf_status icwf_pool_tick(icwf_pool pool, int32_t* n_live, int32_t* n_finished)
   if (graphs) {
     std::vector<int64_t> key;
     for (int id : run) key.push_back(2 * (int64_t)id + pool->jobs[id].h->cur);
-    cudaGraphExec_t exec = nullptr;
+    icwf_pool_ctx::TickExec te;
     auto it = pool->ticks_cache.find(key);
     if (it != pool->ticks_cache.end()) {
-      exec = it->second;
-    } else {
-      cudaGraph_t tg = nullptr;
-      bool ok = cudaGraphCreate(&tg, 0) == cudaSuccess;
-      for (size_t k = 0; ok && k < run.size(); ++k) {
-        PoolJob& j = pool->jobs[run[k]];
-        cudaGraphNode_t node;
-        ok = cudaGraphAddChildGraphNode(&node, tg, nullptr, 0, j.g[j.h->cur]) == cudaSuccess;
-      }
-      ok = ok && cudaGraphInstantiate(&exec, tg, 0) == cudaSuccess;
-      if (tg) cudaGraphDestroy(tg);
-      if (ok) {
-        pool->ticks_cache[key] = exec;
-        pool->stats.graph_builds += 1;
-      } else {
-        exec = nullptr;
-        cudaGetLastError();
-      }
+      te = it->second;
+    } else if (build_tick(pool, run, pool->use_groups, &te)) {
+      pool->ticks_cache[key] = te;
+      pool->stats.graph_builds += 1;
     }
-    if (exec && cudaGraphLaunch(exec, pool->stream) == cudaSuccess) {
+    if (te.exec && cudaGraphLaunch(te.exec, pool->stream) == cudaSuccess) {
       launched = true;
       pool->stats.graph_launches += 1;
+      pool->stats.group_nodes += te.group_nodes;
+      pool->stats.kernel_nodes += te.group_nodes;
       for (int id : run) {
         PoolJob& j = pool->jobs[id];
         icwf_ctx* h = j.h;

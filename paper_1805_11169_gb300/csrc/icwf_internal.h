@@ -72,6 +72,31 @@ template <typename T> void launch_propagate(const JobView& j, int threads, cudaS
 template <typename T> void launch_kinetic(const JobView& j, void* out_psi, void* out_chi,
                                           cudaStream_t s);
 
+// Grouped launches over the live jobs of a serving pool (one precision per group).  One entry per
+// job: its view, its coefficients, the clamp bounds and inverse masses the velocity step uses, and
+// where the job's work items start in the group's item lists (jobs sorted by both).
+struct GroupJob {
+  JobView j;
+  const double2* C;
+  double xlo, xhi, Rlo, Rhi;   // first and last cell centres: positions are clamped to them
+  float inv_mx_f, inv_mR_f;    // 1/m in FP32 (the mixed modes' velocity arithmetic)
+  int traj0;                   // first trajectory item of the job (velocities; prefix sum of N)
+  int cwf0;                    // first CWF item of the job (propagation; prefix sum of 2N)
+};
+// The job's entry with traj0 = cwf0 = 0; bounds and masses as launch_velocity computes them.
+GroupJob group_job(const JobView& j, const double2* C);
+// Adds two kernel nodes to `graph`: a persistent velocity kernel over every trajectory of the
+// njobs jobs in `table` (device memory, njobs >= 1, T = their CWF storage type), then a persistent
+// propagation kernel over every CWF of them (a Strang step, as launch_propagate), which depends on
+// the first; the first depends on deps[0..ndeps).  Each CTA loops over work items (a warp per
+// trajectory, a CTA of `threads` per CWF) with a stride of the grid, which is one wave at full
+// occupancy, at most max_ctas CTAs if max_ctas > 0.  nmax = the largest nx or nR of the group.
+// *last receives the propagation node.  False if a node cannot be added.
+template <typename T>
+bool add_group_nodes(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                     const GroupJob* table, int njobs, int total_traj, int total_cwf, int nmax,
+                     int threads, int max_ctas, cudaGraphNode_t* last);
+
 // a5 (FP64): S = S1 o S2 and Heff from the rank-K factors at the current positions.
 void launch_assemble_fp64(const JobView& j, double2* S, double2* H, cudaStream_t s);
 

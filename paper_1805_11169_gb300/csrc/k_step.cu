@@ -14,12 +14,12 @@ namespace icwf {
 
 // ------------------------------------------------------------------------------ velocities
 
+// One warp per trajectory a (all 32 lanes take part; the caller keeps a warp-uniform).
 template <typename T>
-__global__ void __launch_bounds__(256) k_velocity(JobView j, const double2* __restrict__ C,
-                                                  double xlo, double xhi, double Rlo, double Rhi) {
+__device__ __forceinline__ void velocity_warp(const JobView& j, const double2* __restrict__ C,
+                                              double xlo, double xhi, double Rlo, double Rhi,
+                                              int a, int lane) {
   using Z = c_t<T>;
-  const int a = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
   if (a >= j.N) return;
   const double xa = j.x[a], Ra = j.R[a];
   const Stencil sx = lagrange4(xa, j.x_min, j.dx, j.nx);
@@ -98,6 +98,13 @@ __global__ void __launch_bounds__(256) k_velocity(JobView j, const double2* __re
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_velocity(JobView j, const double2* __restrict__ C,
+                                                  double xlo, double xhi, double Rlo, double Rhi) {
+  velocity_warp<T>(j, C, xlo, xhi, Rlo, Rhi, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
+                   threadIdx.x & 31);
+}
+
 // FP32 version for the mixed modes (complex64 CWFs): stencil weights, interpolation and the
 // three sums in FP32 (FP64 arithmetic is slow and long-latency on this GPU); the position update
 // itself stays FP64.  Pinned factor values at the new positions in FP32 as well (the tensor-core
@@ -127,11 +134,12 @@ __device__ __forceinline__ StencilF lagrange4f(double p, double lo, double d, in
   return st;
 }
 
-__global__ void __launch_bounds__(256) k_velocity_f32(JobView j, const double2* __restrict__ C,
-                                                      double xlo, double xhi, double Rlo, double Rhi,
-                                                      float inv_mx, float inv_mR, float* __restrict__ Cf) {
-  const int a = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+// One warp per trajectory a.  The coefficients are read in FP32 from Cf, or, with Cf = NULL,
+// rounded from C on the fly (the same values k_coeff_to_f32 stores).
+__device__ __forceinline__ void velocity_warp_f32(const JobView& j, const double2* __restrict__ C,
+                                                  double xlo, double xhi, double Rlo, double Rhi,
+                                                  float inv_mx, float inv_mR,
+                                                  const float* __restrict__ Cf, int a, int lane) {
   if (a >= j.N) return;
   const double xa = j.x[a], Ra = j.R[a];
   const StencilF sx = lagrange4f(xa, j.x_min, j.dx, j.nx);
@@ -151,7 +159,8 @@ __global__ void __launch_bounds__(256) k_velocity_f32(JobView j, const double2* 
       E2.x = fmaf(sR.w[m], q.x, E2.x);  E2.y = fmaf(sR.w[m], q.y, E2.y);
       G2.x = fmaf(sR.dw[m], q.x, G2.x); G2.y = fmaf(sR.dw[m], q.y, G2.y);
     }
-    const float2 cb = make_float2(Cf[2 * b], Cf[2 * b + 1]);
+    const float2 cb = Cf ? make_float2(Cf[2 * b], Cf[2 * b + 1])
+                         : make_float2((float)C[b].x, (float)C[b].y);
     const float2 c1 = cmul(cb, E1);
     den = cadd(den, cmul(c1, E2));
     nux = cadd(nux, cmul(cmul(cb, G1), E2));
@@ -207,6 +216,13 @@ __global__ void __launch_bounds__(256) k_velocity_f32(JobView j, const double2* 
   }
 }
 
+__global__ void __launch_bounds__(256) k_velocity_f32(JobView j, const double2* __restrict__ C,
+                                                      double xlo, double xhi, double Rlo, double Rhi,
+                                                      float inv_mx, float inv_mR, float* __restrict__ Cf) {
+  velocity_warp_f32(j, C, xlo, xhi, Rlo, Rhi, inv_mx, inv_mR, Cf,
+                    (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), threadIdx.x & 31);
+}
+
 __global__ void k_coeff_to_f32(int N, const double2* __restrict__ C, float* __restrict__ Cf) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < N) { Cf[2 * b] = (float)C[b].x; Cf[2 * b + 1] = (float)C[b].y; }
@@ -240,20 +256,35 @@ __global__ void k_pinned_only(JobView j) {
   }
 }
 
+GroupJob group_job(const JobView& j, const double2* C) {
+  GroupJob q;
+  q.j = j;
+  q.C = C;
+  q.xlo = j.x_min + 0.5 * j.dx;
+  q.xhi = j.x_min + (j.nx - 0.5) * j.dx;
+  q.Rlo = j.R_min + 0.5 * j.dR;
+  q.Rhi = j.R_min + (j.nR - 0.5) * j.dR;
+  q.inv_mx_f = (float)j.inv_mx;
+  q.inv_mR_f = (float)j.inv_mR;
+  q.traj0 = 0;
+  q.cwf0 = 0;
+  return q;
+}
+
 template <typename T>
 void launch_velocity(const JobView& j, const double2* C, cudaStream_t s) {
   const int warps = 8;
   const int grid = (j.N + warps - 1) / warps;
-  const double xlo = j.x_min + 0.5 * j.dx, xhi = j.x_min + (j.nx - 0.5) * j.dx;
-  const double Rlo = j.R_min + 0.5 * j.dR, Rhi = j.R_min + (j.nR - 0.5) * j.dR;
+  const GroupJob q = group_job(j, C);
+  const double xlo = q.xlo, xhi = q.xhi, Rlo = q.Rlo, Rhi = q.Rhi;
   if (C == nullptr) {
     k_pinned_only<<<grid, warps * 32, 0, s>>>(j);
     return;
   }
   if (sizeof(T) == 4 && j.scratch_f32) {
     k_coeff_to_f32<<<(j.N + 255) / 256, 256, 0, s>>>(j.N, C, j.scratch_f32);
-    k_velocity_f32<<<grid, warps * 32, 0, s>>>(j, C, xlo, xhi, Rlo, Rhi, (float)j.inv_mx,
-                                               (float)j.inv_mR, j.scratch_f32);
+    k_velocity_f32<<<grid, warps * 32, 0, s>>>(j, C, xlo, xhi, Rlo, Rhi, q.inv_mx_f, q.inv_mR_f,
+                                               j.scratch_f32);
     return;
   }
   k_velocity<T><<<grid, warps * 32, 0, s>>>(j, C, xlo, xhi, Rlo, Rhi);
@@ -263,17 +294,14 @@ template void launch_velocity<float>(const JobView&, const double2*, cudaStream_
 
 // ------------------------------------------------------------------------------ propagation
 
-// One CTA per CWF: blocks [0, N) advance psi_a, blocks [N, 2N) advance chi_a.  The column and its
-// potential phases live in shared memory (2 n complex).  mode 0: Strang step in place; mode 1:
-// kinetic operator applied, result to out.
+// One CTA per CWF: CWF index a in [0, N) advances psi_a, a in [N, 2N) advances chi_(a-N).  The
+// column and its potential phases live in shared memory buf (2 n complex).  mode 0: Strang step
+// in place; mode 1: kinetic operator applied, result to out.  Every thread of the CTA calls it.
 template <typename T>
-__global__ void __launch_bounds__(512) k_propagate(JobView j, const T* __restrict__ Vt, int mode,
-                                                   void* out_psi, void* out_chi, double kfx,
-                                                   double kfR) {
+__device__ __forceinline__ void propagate_cta(const JobView& j, const T* __restrict__ Vt, int mode,
+                                              void* out_psi, void* out_chi, double kfx, double kfR,
+                                              int a, c_t<T>* buf) {
   using Z = c_t<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Z* buf = (Z*)smem_raw;
-  int a = blockIdx.x;
   const bool xs = a < j.N;
   if (!xs) a -= j.N;
   const int n = xs ? j.nx : j.nR;
@@ -335,6 +363,14 @@ __global__ void __launch_bounds__(512) k_propagate(JobView j, const T* __restric
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(512) k_propagate(JobView j, const T* __restrict__ Vt, int mode,
+                                                   void* out_psi, void* out_chi, double kfx,
+                                                   double kfR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  propagate_cta<T>(j, Vt, mode, out_psi, out_chi, kfx, kfR, blockIdx.x, (c_t<T>*)smem_raw);
+}
+
 // The propagator's dynamic shared memory limit, set once (to the largest grid's need) so that no
 // launch, captured or not, changes a function attribute.
 template <typename T>
@@ -370,6 +406,106 @@ template void launch_propagate<double>(const JobView&, int, cudaStream_t);
 template void launch_propagate<float>(const JobView&, int, cudaStream_t);
 template void launch_kinetic<double>(const JobView&, void*, void*, cudaStream_t);
 template void launch_kinetic<float>(const JobView&, void*, void*, cudaStream_t);
+
+// ------------------------------------------------------------------------------ grouped launches
+
+// Index of the job whose item range holds `item` (binary search over the sorted starts).
+__device__ __forceinline__ int group_find(const GroupJob* __restrict__ g, int njobs, int item,
+                                          bool cwf) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int start = cwf ? g[mid].cwf0 : g[mid].traj0;
+    if (start <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Velocities, positions and pinned factor values of every trajectory of every job in the group:
+// a warp per trajectory, the warps striding over all trajectories of the group.  The mixed modes
+// round C to FP32 on the fly (the values launch_velocity's k_coeff_to_f32 would store).
+template <typename T>
+__global__ void __launch_bounds__(256) k_velocity_group(const GroupJob* __restrict__ g, int njobs,
+                                                        int total) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)(gridDim.x * (blockDim.x >> 5));
+  for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < total; item += nw) {
+    const GroupJob& q = g[group_find(g, njobs, item, false)];
+    if constexpr (sizeof(T) == 4)
+      velocity_warp_f32(q.j, q.C, q.xlo, q.xhi, q.Rlo, q.Rhi, q.inv_mx_f, q.inv_mR_f, nullptr,
+                        item - q.traj0, lane);
+    else
+      velocity_warp<T>(q.j, q.C, q.xlo, q.xhi, q.Rlo, q.Rhi, item - q.traj0, lane);
+  }
+}
+
+// Strang step of every CWF of every job in the group: a CTA per CWF, the CTAs striding over all
+// CWFs of the group; dynamic shared memory sized for the group's largest grid.
+template <typename T>
+__global__ void __launch_bounds__(512) k_propagate_group(const GroupJob* __restrict__ g, int njobs,
+                                                         int total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const GroupJob& q = g[group_find(g, njobs, item, true)];
+    propagate_cta<T>(q.j, (const T*)q.j.Vt, 0, nullptr, nullptr, 0.0, 0.0, item - q.cwf0,
+                     (c_t<T>*)smem_raw);
+    __syncthreads();   // the next item overwrites the shared column
+  }
+}
+
+template <typename T>
+bool add_group_nodes(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                     const GroupJob* table, int njobs, int total_traj, int total_cwf, int nmax,
+                     int threads, int max_ctas, cudaGraphNode_t* last) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_propagate_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * 4096 * sizeof(c_t<T>))) != cudaSuccess)
+      return false;
+    attr = true;
+  }
+  if (njobs < 1 || total_traj < 1 || total_cwf < 1 || nmax < 1 || nmax > 4096 || threads < 64 ||
+      threads > 512)
+    return false;
+  int dev = 0, sms = 0, occ_v = 0, occ_p = 0;
+  const size_t sm = 2 * (size_t)nmax * sizeof(c_t<T>);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_v, k_velocity_group<T>, 256, 0) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_propagate_group<T>, threads, sm) !=
+          cudaSuccess)
+    return false;
+  if (occ_v < 1 || occ_p < 1) return false;
+  long long gv = ((long long)total_traj + 7) / 8, gp = total_cwf;
+  if (gv > (long long)occ_v * sms) gv = (long long)occ_v * sms;
+  if (gp > (long long)occ_p * sms) gp = (long long)occ_p * sms;
+  if (max_ctas > 0 && gv > max_ctas) gv = max_ctas;
+  if (max_ctas > 0 && gp > max_ctas) gp = max_ctas;
+  cudaKernelNodeParams kp = {};
+  void* av[] = {(void*)&table, (void*)&njobs, (void*)&total_traj};
+  kp.func = (void*)k_velocity_group<T>;
+  kp.gridDim = dim3((unsigned)gv);
+  kp.blockDim = dim3(256);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = av;
+  cudaGraphNode_t nv, np;
+  if (cudaGraphAddKernelNode(&nv, graph, deps, ndeps, &kp) != cudaSuccess) return false;
+  void* ap[] = {(void*)&table, (void*)&njobs, (void*)&total_cwf};
+  kp.func = (void*)k_propagate_group<T>;
+  kp.gridDim = dim3((unsigned)gp);
+  kp.blockDim = dim3((unsigned)threads);
+  kp.sharedMemBytes = (unsigned)sm;
+  kp.kernelParams = ap;
+  if (cudaGraphAddKernelNode(&np, graph, &nv, 1, &kp) != cudaSuccess) return false;
+  *last = np;
+  return true;
+}
+template bool add_group_nodes<double>(cudaGraph_t, const cudaGraphNode_t*, size_t,
+                                      const GroupJob*, int, int, int, int, int, int,
+                                      cudaGraphNode_t*);
+template bool add_group_nodes<float>(cudaGraph_t, const cudaGraphNode_t*, size_t, const GroupJob*,
+                                     int, int, int, int, int, int, cudaGraphNode_t*);
 
 // ------------------------------------------------------------------------------ FP64 assembly
 

@@ -63,6 +63,8 @@ def test_null_handle_calls_are_rejected(lib):
     assert g.LIB.icwf_step(None, 1) == g.ICWF_ERR_ARG
     assert g.LIB.icwf_destroy(None) == g.ICWF_OK
     assert g.LIB.icwf_pool_destroy(None) == g.ICWF_OK
+    assert g.LIB.icwf_pool_set_grouping(None, 1, 0) == g.ICWF_ERR_ARG
+    assert g.LIB.icwf_pool_set_graphs(None, 1) == g.ICWF_ERR_ARG
 
 
 def test_exact2d_rejects_bad_arguments_without_a_gpu(lib):

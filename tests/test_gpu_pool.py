@@ -46,6 +46,48 @@ def _same(a, b):
     assert abs(a["t"] - b["t"]) < 1e-12
 
 
+def _group_nodes(jobs):
+    """Grouped kernels a graph-ticked run of `jobs` (all admitted at the first tick) executes:
+    at tick t, two for each CWF precision (FP64 or complex64) among the jobs still stepping."""
+    total = 0
+    for t in range(1, max(n for *_r, n in jobs) + 1):
+        total += 2 * len({prec == 0 for _w, prec, _s, n in jobs if n >= t})
+    return total
+
+
+def _run_pool(jobs, max_live, graphs=True, grouping=None):
+    pool = g.icwf_pool_create(1 << 34, max_live)
+    g.icwf_pool_set_graphs(pool, graphs)
+    if grouping is not None:
+        g.icwf_pool_set_grouping(pool, *grouping)
+    ids = [g.icwf_pool_submit(pool, _make(w, prec, seed).release(), n) for w, prec, seed, n in jobs]
+    for _ in range(200):
+        live, _ = g.icwf_pool_tick(pool)
+        if live == 0 and all(g.icwf_pool_poll(pool, i, w.nx, w.nR)[0] == 2
+                             for i, (w, *_r) in zip(ids, jobs)):
+            break
+    out = [g.icwf_pool_poll(pool, i, w.nx, w.nR) for i, (w, *_r) in zip(ids, jobs)]
+    st = g.icwf_pool_get_stats(pool)
+    g.icwf_pool_destroy(pool)
+    assert all(s == 2 for s, _o in out), [s for s, _o in out]
+    return [o for _s, o in out], st
+
+
+def test_grouped_kernels_loop_over_all_jobs():
+    """The grouped velocity and propagation kernels stride over the work items of every live job:
+    capped at 3 CTAs each (every CTA then handles CWFs and trajectories of several jobs, with
+    ragged N and grids), with no cap, and with grouping off, the results equal direct launches."""
+    jobs = _jobs()
+    ref, st = _run_pool(jobs, 5, graphs=False)
+    assert st["group_nodes"] == 0
+    for grouping in ((True, 3), (True, 0), (False, 0)):
+        res, st = _run_pool(jobs, 5, graphs=True, grouping=grouping)
+        assert st["eager_job_steps"] == 0
+        assert st["group_nodes"] == (_group_nodes(jobs) if grouping[0] else 0)
+        for a, b in zip(res, ref):
+            _same(a, b)
+
+
 def test_each_job_is_the_same_alone_and_in_the_mix():
     jobs = _jobs()
     alone = []
@@ -135,8 +177,12 @@ def test_graph_ticks_equal_eager_ticks_and_launch_once_per_tick():
             assert st["graph_launches"] == stepping_ticks
             assert st["kernel_nodes"] > 10 * st["graph_job_steps"]
             assert st["graph_builds"] <= 2 * len(jobs)
+            # two grouped kernels (velocities, propagation) per CWF precision live in the tick,
+            # however many jobs of that precision there are
+            assert st["group_nodes"] == _group_nodes(jobs)
         else:
             assert st["graph_launches"] == 0 and st["eager_job_steps"] == sum(n for *_r, n in jobs)
+            assert st["group_nodes"] == 0
         g.icwf_pool_destroy(pool)
     for a, b in zip(results[True], results[False]):
         _same(a, b)
