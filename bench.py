@@ -806,11 +806,44 @@ def _run_stream(lib, jobs, arrivals, graphs, max_live, precision, grouping=True)
             "eager_job_steps": stats["eager_job_steps"]}, results
 
 
+def _run_saturated(lib, jobs, max_live, precision, grouping):
+    """Capacity: every job created first, all submitted at once, the pool ticked until all are
+    done; aggregate trajectory-steps/s over the makespan of the ticks."""
+    import paper_1805_11169_gb300 as g
+    made = [_make_job(lib, job, precision) for job in jobs]
+    pool = g.icwf_pool_create(64 << 30, max_live)
+    g.icwf_pool_set_grouping(pool, grouping, 0)
+    ids = [g.icwf_pool_submit(pool, sim.release(), job["steps"])
+           for (sim, _w), job in zip(made, jobs)]
+    grids = [(w.nx, w.nR) for _sim, w in made]
+
+    def states():
+        return [g.icwf_pool_poll(pool, i, *grid)[0] for i, grid in zip(ids, grids)]
+
+    t0 = time.perf_counter()
+    while True:
+        live, _ = g.icwf_pool_tick(pool)
+        if live == 0 and all(st in (2, 3) for st in states()):
+            break
+    makespan = time.perf_counter() - t0
+    failed = sum(1 for st in states() if st == 3)
+    stats = g.icwf_pool_get_stats(pool)
+    g.icwf_pool_destroy(pool)
+    ts = sum(j["N"] * j["steps"] for j in jobs)
+    return {"traj_steps_per_s": ts / makespan, "makespan_s": makespan, "failed": failed,
+            "ticks": stats["ticks"],
+            "kernels_per_graph_launch": (stats["kernel_nodes"] / stats["graph_launches"]
+                                         if stats["graph_launches"] else None),
+            "grouped_kernels_per_graph_launch": (stats["group_nodes"] / stats["graph_launches"]
+                                                 if stats["graph_launches"] else None)}
+
+
 def run_serving(n_jobs, mode="tf32x3", seed=0, load=0.7, max_live=16, n_checked=4):
     """Poisson stream of mixed-size jobs (N up to 2048) through the pool (continuous batching),
     with captured tick graphs and grouped velocity/propagation kernels over all live jobs (the
-    default), with tick graphs of per-job kernels only, and with direct launches: job latency
-    p50/p99 (arrival -> result on the host), aggregate trajectory-steps/s and launches per tick.
+    default) and with direct launches: job latency p50/p99 (arrival -> result on the host),
+    aggregate trajectory-steps/s and launches per tick.  The same jobs submitted all at once
+    measure the pool's capacity, with and without the grouped kernels (`saturated`).
     Jobs' mixed-precision results are checked against FP64 runs of the same jobs (a sample of the
     small ones: the FP64 path is ~50x slower)."""
     import numpy as np
@@ -830,8 +863,9 @@ def run_serving(n_jobs, mode="tf32x3", seed=0, load=0.7, max_live=16, n_checked=
     rate = load / mean_service
     arrivals = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / rate, n_jobs))
     graphs, res = _run_stream(lib, jobs, arrivals, True, max_live, prec)
-    ungrouped, _ = _run_stream(lib, jobs, arrivals, True, max_live, prec, grouping=False)
     eager, _ = _run_stream(lib, jobs, arrivals, False, max_live, prec)
+    saturated = {("grouped" if gr else "ungrouped"): _run_saturated(lib, jobs, max_live, prec, gr)
+                 for gr in (True, False)}
     # precision check: the first n_checked jobs with N <= 256, in FP64, same seed, alone
     checks = []
     for j, job in enumerate(jobs):
@@ -850,8 +884,8 @@ def run_serving(n_jobs, mode="tf32x3", seed=0, load=0.7, max_live=16, n_checked=
                        "rho_R_L1": float(w.dR * np.sum(np.abs(ob["rho_R"] - ref["rho_R"]))),
                        "pop_L1": float(np.sum(np.abs(ob["pop"] - ref["pop"])))})
     return {"jobs": n_jobs, "p50_s": graphs["p50_s"], "p99_s": graphs["p99_s"],
-            "traj_steps_per_s": graphs["traj_steps_per_s"], "graphs": graphs,
-            "graphs_ungrouped": ungrouped, "eager": eager,
+            "traj_steps_per_s": graphs["traj_steps_per_s"], "graphs": graphs, "eager": eager,
+            "saturated": saturated,
             "arrival_rate_per_s": rate, "max_live": max_live, "precision": MODES[mode][1],
             "vs_fp64": checks,
             "stream": "Poisson arrivals; Shin-Metiu (3 grids, dt 0.05, eps 1e-6) and cavity "

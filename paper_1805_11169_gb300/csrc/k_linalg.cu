@@ -19,12 +19,12 @@ constexpr unsigned WAIT_LIMIT = 1u << 22;   // bounded spin (x ~64 ns sleep: wel
 
 // ------------------------------------------------------------------------------ S + eps I
 
+// One CTA per row r (no index division per element).
 __global__ void k_shift_mix(int N, const double2* __restrict__ S0, const double2* __restrict__ S1,
                             double eps, double theta, double2* __restrict__ A) {
-  const size_t NN = (size_t)N * N;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < NN;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = e / N, c = e % N;
+  const int r = blockIdx.x;
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    const size_t e = (size_t)r * N + c;
     double2 v;
     if (theta == 1.0) {
       v = S1[e];
@@ -40,10 +40,7 @@ __global__ void k_shift_mix(int N, const double2* __restrict__ S0, const double2
 
 void launch_shift_mix(int N, const double2* S0, const double2* S1, double eps, double theta,
                       double2* A, cudaStream_t s) {
-  const size_t NN = (size_t)N * N;
-  size_t g = (NN + 255) / 256;
-  if (g > 4096) g = 4096;
-  k_shift_mix<<<(unsigned)g, 256, 0, s>>>(N, S0, S1, eps, theta, A);
+  k_shift_mix<<<N, 256, 0, s>>>(N, S0, S1, eps, theta, A);
 }
 
 // ------------------------------------------------------------------------------ Cholesky

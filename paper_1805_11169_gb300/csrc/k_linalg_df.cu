@@ -117,12 +117,12 @@ __device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
 
 // ---------------------------------------------------------------------------- S + eps I
 
+// One CTA per row r (no index division per element).
 __global__ void k_shift_mix_df(int N, const double2* __restrict__ S0, const double2* __restrict__ S1,
                                double eps, double theta, float4* __restrict__ A) {
-  const size_t NN = (size_t)N * N;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < NN;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = e / N, c = e % N;
+  const int r = blockIdx.x;
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    const size_t e = (size_t)r * N + c;
     double2 v;
     if (theta == 1.0) v = S1[e];
     else if (theta == 0.0) v = S0[e];
@@ -1148,10 +1148,7 @@ size_t cluster_solve_smem(int N) { return clayout_bytes((N + NB - 1) / NB); }
 
 void launch_shift_mix_df(int N, const double2* S0, const double2* S1, double eps, double theta,
                          void* A, cudaStream_t s) {
-  const size_t NN = (size_t)N * N;
-  size_t g = (NN + 255) / 256;
-  if (g > 4096) g = 4096;
-  dfs::k_shift_mix_df<<<(unsigned)g, 256, 0, s>>>(N, S0, S1, eps, theta, (float4*)A);
+  dfs::k_shift_mix_df<<<N, 256, 0, s>>>(N, S0, S1, eps, theta, (float4*)A);
 }
 
 int launch_cholesky_df(int N, void* const* A, void* const* inv, void* const* D, int nbatch,

@@ -8,16 +8,19 @@
 #include <cuda_runtime.h>
 
 #include "icwf_internal.h"
+#include "df64.cuh"
 #include "k_common.cuh"
 
 namespace icwf {
 
 constexpr int RT = 32;   // reconstruction tile (grid points)
-constexpr int RC = 16;   // trajectories per staged chunk
+constexpr int RC = 16;   // trajectories per staged chunk (FP64 CWFs)
+constexpr int RCF = 32;  // trajectories per staged chunk (complex64 CWFs)
 
+// FP64 CWFs: every product and sum in FP64.
 template <typename T>
-__global__ void __launch_bounds__(256) k_reconstruct(JobView j, const double2* __restrict__ C,
-                                                     double2* __restrict__ Psi) {
+__device__ __forceinline__ void reconstruct_fp64(const JobView& j, const double2* __restrict__ C,
+                                                 double2* __restrict__ Psi) {
   using Z = c_t<T>;
   __shared__ double2 P[RC][RT + 1];
   __shared__ double2 Q[RC][RT + 1];
@@ -59,6 +62,83 @@ __global__ void __launch_bounds__(256) k_reconstruct(JobView j, const double2* _
       const int i = it * RT + ty + 16 * r, jj = jt * RT + tx + 16 * c;
       if (i < j.nx && jj < j.nR) Psi[(size_t)i * j.nR + jj] = acc[r][c];
     }
+}
+
+// Complex64 CWFs (mixed modes): the terms C_a psi_a(x_i) chi_a(R_j) and their sums over chunks of
+// RCF trajectories in FP32 (C rounded to FP32; the CWFs carry FP32 rounding already), the chunk
+// sums added error-free into double-float accumulators (TwoSum), the result written in FP64.
+// FP64 arithmetic would bound this GEMM-shaped sum on this GPU (~1/60 of the FP32 rate).  On the
+// Shin-Metiu bench grid (N = 256 and 1024, where the terms' magnitudes add up to ~25-50x |Psi|)
+// this changes rho_x, rho_R, P_n and the norm by < 2e-7 (L1) against FP64 sums of the same
+// complex64 CWFs.
+__device__ __forceinline__ void reconstruct_f32(const JobView& j, const double2* __restrict__ C,
+                                                double2* __restrict__ Psi) {
+  __shared__ float2 P[RCF][RT + 1];
+  __shared__ float2 Q[RCF][RT + 1];
+  __shared__ float2 Cs[RCF];
+  const int it = blockIdx.y, jt = blockIdx.x;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const float2* psi = (const float2*)j.psi;
+  const float2* chi = (const float2*)j.chi;
+  const float2 z = make_float2(0.f, 0.f);
+  df acc[2][2][2];   // [row][column][re, im]
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) acc[r][c][0] = acc[r][c][1] = df_make(0.f, 0.f);
+  const int la = threadIdx.x >> 5;          // 0..7: trajectory within chunk (four passes)
+  const int lp = threadIdx.x & 31;          // grid point within tile
+  const int i = it * RT + lp, jj = jt * RT + lp;
+  for (int a0 = 0; a0 < j.N; a0 += RCF) {
+    if (threadIdx.x < RCF) {
+      const int a = a0 + threadIdx.x;
+      Cs[threadIdx.x] = a < j.N ? make_float2((float)C[a].x, (float)C[a].y) : z;
+    }
+#pragma unroll
+    for (int q = 0; q < RCF / 8; ++q) {
+      const int a = a0 + la + 8 * q;
+      float2 p = z, w = z;
+      if (a < j.N) {
+        if (i < j.nx) p = psi[(size_t)a * j.nx + i];
+        if (jj < j.nR) w = chi[(size_t)a * j.nR + jj];
+      }
+      P[la + 8 * q][lp] = p;
+      Q[la + 8 * q][lp] = w;
+    }
+    __syncthreads();
+    float2 s[2][2] = {{z, z}, {z, z}};
+#pragma unroll 8
+    for (int a = 0; a < RCF; ++a) {
+      const float2 c = Cs[a];
+      const float2 p0 = cmul(c, P[a][ty]), p1 = cmul(c, P[a][ty + 16]);
+      const float2 q0 = Q[a][tx], q1 = Q[a][tx + 16];
+      cfma(s[0][0], p0, q0); cfma(s[0][1], p0, q1);
+      cfma(s[1][0], p1, q0); cfma(s[1][1], p1, q1);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        acc[r][c][0] = df_add_f(acc[r][c][0], s[r][c].x);
+        acc[r][c][1] = df_add_f(acc[r][c][1], s[r][c].y);
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int ii = it * RT + ty + 16 * r, jc = jt * RT + tx + 16 * c;
+      if (ii < j.nx && jc < j.nR)
+        Psi[(size_t)ii * j.nR + jc] = make_double2(df_to(acc[r][c][0]), df_to(acc[r][c][1]));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_reconstruct(JobView j, const double2* __restrict__ C,
+                                                     double2* __restrict__ Psi) {
+  if constexpr (sizeof(T) == 4) reconstruct_f32(j, C, Psi);
+  else reconstruct_fp64<T>(j, C, Psi);
 }
 
 template <typename T>

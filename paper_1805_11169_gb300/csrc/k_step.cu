@@ -134,8 +134,9 @@ __device__ __forceinline__ StencilF lagrange4f(double p, double lo, double d, in
   return st;
 }
 
-// One warp per trajectory a.  The coefficients are read in FP32 from Cf, or, with Cf = NULL,
-// rounded from C on the fly (the same values k_coeff_to_f32 stores).
+// One warp per trajectory a.  The coefficients are read in FP32 from Cf, or, with kFromC, rounded
+// from C on the fly (the same values k_coeff_to_f32 stores in Cf).
+template <bool kFromC>
 __device__ __forceinline__ void velocity_warp_f32(const JobView& j, const double2* __restrict__ C,
                                                   double xlo, double xhi, double Rlo, double Rhi,
                                                   float inv_mx, float inv_mR,
@@ -159,8 +160,8 @@ __device__ __forceinline__ void velocity_warp_f32(const JobView& j, const double
       E2.x = fmaf(sR.w[m], q.x, E2.x);  E2.y = fmaf(sR.w[m], q.y, E2.y);
       G2.x = fmaf(sR.dw[m], q.x, G2.x); G2.y = fmaf(sR.dw[m], q.y, G2.y);
     }
-    const float2 cb = Cf ? make_float2(Cf[2 * b], Cf[2 * b + 1])
-                         : make_float2((float)C[b].x, (float)C[b].y);
+    const float2 cb = kFromC ? make_float2((float)C[b].x, (float)C[b].y)
+                             : make_float2(Cf[2 * b], Cf[2 * b + 1]);
     const float2 c1 = cmul(cb, E1);
     den = cadd(den, cmul(c1, E2));
     nux = cadd(nux, cmul(cmul(cb, G1), E2));
@@ -219,8 +220,8 @@ __device__ __forceinline__ void velocity_warp_f32(const JobView& j, const double
 __global__ void __launch_bounds__(256) k_velocity_f32(JobView j, const double2* __restrict__ C,
                                                       double xlo, double xhi, double Rlo, double Rhi,
                                                       float inv_mx, float inv_mR, float* __restrict__ Cf) {
-  velocity_warp_f32(j, C, xlo, xhi, Rlo, Rhi, inv_mx, inv_mR, Cf,
-                    (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), threadIdx.x & 31);
+  velocity_warp_f32<false>(j, C, xlo, xhi, Rlo, Rhi, inv_mx, inv_mR, Cf,
+                           (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), threadIdx.x & 31);
 }
 
 __global__ void k_coeff_to_f32(int N, const double2* __restrict__ C, float* __restrict__ Cf) {
@@ -432,8 +433,8 @@ __global__ void __launch_bounds__(256) k_velocity_group(const GroupJob* __restri
   for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < total; item += nw) {
     const GroupJob& q = g[group_find(g, njobs, item, false)];
     if constexpr (sizeof(T) == 4)
-      velocity_warp_f32(q.j, q.C, q.xlo, q.xhi, q.Rlo, q.Rhi, q.inv_mx_f, q.inv_mR_f, nullptr,
-                        item - q.traj0, lane);
+      velocity_warp_f32<true>(q.j, q.C, q.xlo, q.xhi, q.Rlo, q.Rhi, q.inv_mx_f, q.inv_mR_f,
+                              nullptr, item - q.traj0, lane);
     else
       velocity_warp<T>(q.j, q.C, q.xlo, q.xhi, q.Rlo, q.Rhi, item - q.traj0, lane);
   }
