@@ -436,27 +436,40 @@ def run_ours(args, rank, ws, local):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = run_e2e(args, w, params, g)
+        record(out, "e2e", run_e2e, args, w, params, g)
     if rank == 0 and not args.no_fp64 and args.mode != "fp64":
-        out["fp64"] = run_fp64_comparison()
-        out["speedup_vs_fp64"] = value / out["fp64"]["value"]
+        if record(out, "fp64", run_fp64_comparison):
+            out["speedup_vs_fp64"] = value / out["fp64"]["value"]
     if rank == 0 and not args.no_extras and args.workload == "shin_metiu":
-        out["rank_error"] = run_rank_error(args.mode)
+        record(out, "rank_error", run_rank_error, args.mode)
         if args.mode != "fp64":
-            out["mixed_vs_fp64"] = run_mixed_vs_fp64(args.mode, eps)
+            record(out, "mixed_vs_fp64", run_mixed_vs_fp64, args.mode, eps)
             if args.solve != "fp64":
-                out["solve_fp64"] = run_solve_fp64(args.mode, eps, local)
-        out["cavity"] = run_cavity_line(args, local, peaks)
+                record(out, "solve_fp64", run_solve_fp64, args.mode, eps, local)
+        record(out, "cavity", run_cavity_line, args, local, peaks)
     if rank == 0 and not args.no_exact2d:
-        out["exact2d"] = run_exact2d(w)
+        record(out, "exact2d", run_exact2d, w)
     if rank == 0 and args.vs_exact > 0:
-        out["vs_exact"] = run_vs_exact(w, prec, args.vs_exact, args.vs_exact_every, w.seed,
-                                       int(args.overlap_split))
+        record(out, "vs_exact", run_vs_exact, w, prec, args.vs_exact, args.vs_exact_every, w.seed,
+               int(args.overlap_split))
     if rank == 0 and args.serving_jobs > 0:
-        out["serving"] = run_serving(args.serving_jobs, args.mode if args.mode != "fp64" else "tf32x3")
+        record(out, "serving", run_serving, args.serving_jobs,
+               args.mode if args.mode != "fp64" else "tf32x3")
     if rank == 0 and not args.no_cpu:
-        out["cpu_baseline"] = run_cpu_baseline(w, args.cpu_budget_s)
+        record(out, "cpu_baseline", run_cpu_baseline, w, args.cpu_budget_s)
     return out
+
+
+def record(out, key, fn, *fargs):
+    """out[key] = fn(*fargs); a record that fails is reported in the line as {"error": ...} (and
+    on stderr) instead of losing the headline measured before it.  True if it succeeded."""
+    try:
+        out[key] = fn(*fargs)
+        return True
+    except Exception as e:  # noqa: BLE001 -- any failure of an extra record is reported, not raised
+        out[key] = {"error": f"{type(e).__name__}: {e}"}
+        log(f"{key} failed: {type(e).__name__}: {e}")
+        return False
 
 
 def run_e2e(args, w, params, g):

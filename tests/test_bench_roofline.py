@@ -59,3 +59,17 @@ def test_measured_peaks_file_has_the_keys_bench_reads():
         pytest.skip("MEASURED_PEAKS.json is written per pool")
     p = json.load(open(path))
     assert p["hbm_gbs"] > 0 and p["bf16_tflops_sustained"] > 0
+
+
+def test_a_failing_extra_record_keeps_the_line():
+    """An extra record that raises is reported in the line as an error; the others still run."""
+    out = {"value": 1.0}
+
+    def boom():
+        raise RuntimeError("no device")
+
+    assert not bench.record(out, "serving", boom)
+    assert bench.record(out, "exact2d", lambda a, b: {"value": a + b}, 2, 3)
+    assert out["serving"] == {"error": "RuntimeError: no device"}
+    assert out["exact2d"] == {"value": 5} and out["value"] == 1.0
+    json.dumps(out)
