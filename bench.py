@@ -481,6 +481,7 @@ def run_e2e(args, w, params, g):
     sim = g.Icwf(params, w.V)
     sim.set_projectors(w.phi)
     sim.init_from_density(w.psi0, w.seed)
+    t1 = time.perf_counter()
     n_obs = 0
     done = 0
     while done < args.steps:
@@ -490,6 +491,7 @@ def run_e2e(args, w, params, g):
         if done % OBS_EVERY == 0 or done == args.steps:
             sim.observables()
             n_obs += 1
+    t2 = time.perf_counter()
     sim.close()
     dt = time.perf_counter() - t0
     h2d = w.V.nbytes + w.phi.nbytes + w.psi0.nbytes
@@ -497,7 +499,11 @@ def run_e2e(args, w, params, g):
     return {"value": w.n_traj * args.steps / dt, "unit": "trajectory-steps/s",
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
             "wall_s": dt, "includes": "create (host SVD of V), init (sampling, slices, C0), steps, "
-                                      "observables copies, destroy"}
+                                      "observables copies, destroy",
+            "setup_s": t1 - t0,
+            "steps_value": w.n_traj * args.steps / (t2 - t1),
+            "steps_value_includes": "icwf_step and icwf_observables (results copied to host "
+                                    "arrays) only, after create and init"}
 
 
 def run_cpu_baseline(w, budget_s):
