@@ -105,35 +105,10 @@ __global__ void __launch_bounds__(256) k_velocity(JobView j, const double2* __re
                    threadIdx.x & 31);
 }
 
-// FP32 version for the mixed modes (complex64 CWFs): stencil weights, interpolation and the
-// three sums in FP32 (FP64 arithmetic is slow and long-latency on this GPU); the position update
-// itself stays FP64.  Pinned factor values at the new positions in FP32 as well (the tensor-core
-// assembly consumes them in FP32).
-struct StencilF {
-  int i0;
-  float w[4];
-  float dw[4];
-};
-__device__ __forceinline__ StencilF lagrange4f(double p, double lo, double d, int n) {
-  StencilF st;
-  const float s = (float)((p - lo) / d) - 0.5f;
-  int i0 = (int)floorf(s) - 1;
-  i0 = i0 < 0 ? 0 : (i0 > n - 4 ? n - 4 : i0);
-  const float u = s - (float)i0;
-  const float u1 = u - 1.f, u2 = u - 2.f, u3 = u - 3.f;
-  const float inv = (float)(1.0 / d);
-  st.i0 = i0;
-  st.w[0] = -(u1 * u2 * u3) * (1.f / 6.f);
-  st.w[1] = (u * u2 * u3) * 0.5f;
-  st.w[2] = -(u * u1 * u3) * 0.5f;
-  st.w[3] = (u * u1 * u2) * (1.f / 6.f);
-  st.dw[0] = -((u2 * u3) + (u1 * u3) + (u1 * u2)) * (1.f / 6.f) * inv;
-  st.dw[1] = ((u2 * u3) + (u * u3) + (u * u2)) * 0.5f * inv;
-  st.dw[2] = -((u1 * u3) + (u * u3) + (u * u1)) * 0.5f * inv;
-  st.dw[3] = ((u1 * u2) + (u * u2) + (u * u1)) * (1.f / 6.f) * inv;
-  return st;
-}
-
+// FP32 version for the mixed modes (complex64 CWFs): stencil weights (lagrange4f), interpolation
+// and the three sums in FP32 (FP64 arithmetic is slow and long-latency on this GPU); the position
+// update itself stays FP64.  Pinned factor values at the new positions in FP32 as well (the
+// tensor-core assembly consumes them in FP32).
 // One warp per trajectory a.  The coefficients are read in FP32 from Cf, or, with kFromC, rounded
 // from C on the fly (the same values k_coeff_to_f32 stores in Cf).
 template <bool kFromC>
