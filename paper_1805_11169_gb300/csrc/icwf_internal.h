@@ -85,6 +85,19 @@ struct GroupJob {
 };
 // The job's entry with traj0 = cwf0 = 0; bounds and masses as launch_velocity computes them.
 GroupJob group_job(const JobView& j, const double2* C);
+// Index of the job whose item range holds `item` (0 <= item < the group's total): binary search
+// over the jobs' starts (traj0, or cwf0 with `cwf`), which increase strictly since every job has
+// N >= 1.  Host and device code.
+__host__ __device__ inline int group_find(const GroupJob* __restrict__ g, int njobs, int item,
+                                          bool cwf) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int start = cwf ? g[mid].cwf0 : g[mid].traj0;
+    if (start <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 // Adds two kernel nodes to `graph`: a persistent velocity kernel over every trajectory of the
 // njobs jobs in `table` (device memory, njobs >= 1, T = their CWF storage type), then a persistent
 // propagation kernel over every CWF of them (a Strang step, as launch_propagate), which depends on

@@ -385,18 +385,6 @@ template void launch_kinetic<float>(const JobView&, void*, void*, cudaStream_t);
 
 // ------------------------------------------------------------------------------ grouped launches
 
-// Index of the job whose item range holds `item` (binary search over the sorted starts).
-__device__ __forceinline__ int group_find(const GroupJob* __restrict__ g, int njobs, int item,
-                                          bool cwf) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    const int start = cwf ? g[mid].cwf0 : g[mid].traj0;
-    if (start <= item) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Velocities, positions and pinned factor values of every trajectory of every job in the group:
 // a warp per trajectory, the warps striding over all trajectories of the group.  The mixed modes
 // round C to FP32 on the fly (the values launch_velocity's k_coeff_to_f32 would store).
